@@ -1,0 +1,222 @@
+/*
+ * hipermotif.h -- C ABI of the GB300 (sm_103a) subgraph-matching library.
+ *
+ * The library finds every match of a small labelled pattern graph G1 in a
+ * large labelled target digraph G2 (Sec. II-A): every injective
+ * f : V1 -> V2 with equal vertex labels (Eq. 2), every pattern arc mapped to a
+ * target arc with an equal label (Eq. 3), and, in induced mode, no target arc
+ * between the images of a pattern non-arc (Eq. 1, "<=>"); monomorphism keeps
+ * only "=>".  It follows the HiPerMotif method (Sec. III): the pattern is
+ * reordered by degree (Alg. 1); every target arc is tried as the image of the
+ * reordered pattern's first arc (positions 0 and 1); vertex and edge
+ * validators (Alg. 2, Alg. 3) reject candidates; survivors are injected as
+ * depth-2 partial mappings and extended vertex by vertex in parallel (the
+ * HiPerMotif algorithm of Sec. III-C).
+ *
+ * Conventions for every entry point
+ *   - Plain pointers and sizes only.  "host" pointers are ordinary CPU
+ *     memory; "device" pointers are CUDA global memory on the current device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is stream-ordered on it; a call that returns a count on
+ *     the host synchronises with its own copy of that count, nothing more.
+ *   - Every call returns an hm_status and never aborts, traps or exits.  On an
+ *     error no output is written unless the entry point says otherwise.
+ *   - Vertex ids are int32 in [0, n); labels are arbitrary int32 values;
+ *     counts are uint64 (a match is a mapping, so automorphic copies count
+ *     separately).  Rows are written in ORIGINAL pattern-vertex order
+ *     (f(0), ..., f(k-1)) and returned sorted ascending lexicographically.
+ *   - The target must be a simple digraph: no self-loop (u, u) and no
+ *     repeated ordered pair (u, v); the loaders reject anything else.
+ *   - Objects are created on the device that is current at creation and must
+ *     be used with that device current.  hm_graph / hm_pattern objects are
+ *     read-only after creation and may be shared by concurrent calls on
+ *     different streams.
+ */
+#ifndef HIPERMOTIF_H
+#define HIPERMOTIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HM_OK = 0,
+  HM_ERR_ARG = 1,       /* bad pointer, size, id out of range, bad mode      */
+  HM_ERR_SELF_LOOP = 2, /* target or pattern has an arc (u, u)               */
+  HM_ERR_DUP_EDGE = 3,  /* target or pattern repeats an ordered pair (u, v)  */
+  HM_ERR_PATTERN = 4,   /* pattern k < 2, k > HM_MAX_K, no arc, or not weakly connected */
+  HM_ERR_OOM = 5,       /* a device allocation failed                        */
+  HM_ERR_CAPACITY = 6,  /* output buffer too small; *count holds the needed rows */
+  HM_ERR_BUDGET = 7,    /* the device work budget ran out; results invalid   */
+  HM_ERR_CUDA = 8,      /* a CUDA runtime call failed                        */
+  HM_ERR_NO_DEVICE = 9  /* no CUDA device is usable                          */
+} hm_status;
+
+typedef enum { HM_MONO = 0, HM_INDUCED = 1 } hm_mode;
+
+enum { HM_MAX_K = 16 };
+
+typedef struct hm_graph hm_graph;     /* opaque: device-resident target graph  */
+typedef struct hm_pattern hm_pattern; /* opaque: reordered pattern and plans   */
+
+/* Human-readable name of a status (static string, never NULL). */
+const char *hm_status_str(hm_status s);
+
+/* ------------------------------------------------------------------------
+ * Target graph.
+ *
+ * hm_load_graph -- builds the device-resident target (the paper's double-
+ * index storage, Sec. III-D: CSR plus the per-arc source array, and
+ * contiguous attribute arrays) from an arc list.
+ *   n           vertices (>= 0); m arcs (>= 0).
+ *   src, dst    int32[m] arc endpoints; vlab int32[n]; elab int32[m].
+ *   device_ptrs 0: the four arrays are host memory; 1: device memory.
+ *   stream      stream for the build (see conventions).
+ *   out         receives the new graph; the caller frees it with hm_free_graph.
+ * Layout built: out-lists (CSR) sorted by (src, dst) and in-lists (CSC) sorted
+ * by (dst, src), each with its arc labels, the CSR-order source array, and per
+ * vertex {label, out-degree, in-degree} and {out-offset, in-offset}.
+ * The input arrays are copied; the caller keeps ownership.  m must be below
+ * 2^31.  Errors: HM_ERR_ARG (id out of range, n or m negative, m >= 2^31,
+ * NULL array),
+ * HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_OOM, HM_ERR_CUDA.  Synchronises
+ * `stream` before returning.
+ * ------------------------------------------------------------------------ */
+hm_status hm_load_graph(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                        const int32_t *vlab, const int32_t *elab, int device_ptrs,
+                        void *stream, hm_graph **out);
+
+void hm_free_graph(hm_graph *g);
+
+/* Sizes of a loaded graph (host outputs; any may be NULL). */
+hm_status hm_graph_info(const hm_graph *g, int32_t *n, int64_t *m, size_t *device_bytes);
+
+/* Copy the built adjacency back to HOST buffers (for inspection and tests):
+ * out_off/in_off int64[n+1]; out_adj/out_elab/in_adj/in_elab int32[m].
+ * Any pointer may be NULL to skip that array.  Synchronous. */
+hm_status hm_graph_export(const hm_graph *g, int64_t *out_off, int32_t *out_adj,
+                          int32_t *out_elab, int64_t *in_off, int32_t *in_adj,
+                          int32_t *in_elab);
+
+/* Copy the label-grouped adjacency back to HOST buffers (inspection, tests).
+ * Each vertex's out-list (in-list) is also kept ordered by (arc label,
+ * neighbour label, neighbour id); one directory entry per such group.
+ *   gout_adj, gin_adj  int32[m]: the grouped lists (same offsets as the plain ones).
+ *   vdir               int32[4n]: per vertex {first out entry, out entries,
+ *                      first in entry, in entries}.
+ *   gdir_out, gdir_in  int32[4 * entries]: {arc label, neighbour label, first,
+ *                      end}, first/end relative to the vertex's list start.
+ *   ndir               int64[2]: number of out and in entries.
+ * Any pointer may be NULL.  Synchronous. */
+hm_status hm_graph_export_groups(const hm_graph *g, int32_t *gout_adj, int32_t *gin_adj,
+                                 int32_t *vdir, int32_t *gdir_out, int32_t *gdir_in,
+                                 int64_t *ndir);
+
+/* ------------------------------------------------------------------------
+ * Pattern graph.
+ *
+ * hm_load_pattern -- validates the pattern and runs Alg. 1 (Structural
+ * Reordering, Sec. III-A): sigma(v) = (totaldeg, outdeg); the sigma-argmax
+ * takes position 0; each next position takes the sigma-argmax among the
+ * unplaced out-neighbours of the last placed vertex, else among all unplaced
+ * vertices.  Readings where the paper is silent: ties go to the lowest
+ * original id; degrees are static; and if the fallback pick has no arc to a
+ * placed vertex, the sigma-argmax among unplaced vertices that do have one is
+ * taken instead, so every position after 0 is anchored.  It then builds the
+ * per-position plans used by the kernels for both modes.
+ *   k     pattern vertices, 2 <= k <= HM_MAX_K;  mp  pattern arcs (>= 1).
+ *   src, dst int32[mp], vlab int32[k], elab int32[mp]: HOST memory.
+ *   out   receives the pattern; free with hm_free_pattern.  Host-only: needs no GPU.
+ * Errors: HM_ERR_ARG, HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_PATTERN.
+ * ------------------------------------------------------------------------ */
+hm_status hm_load_pattern(int32_t k, int32_t mp, const int32_t *src, const int32_t *dst,
+                          const int32_t *vlab, const int32_t *elab, hm_pattern **out);
+
+void hm_free_pattern(hm_pattern *p);
+
+/* order_out (host int32[k]) receives Alg. 1's result: order_out[i] is the
+ * original pattern vertex placed at position i.  Host-only. */
+hm_status hm_pattern_order(const hm_pattern *p, int32_t *order_out);
+
+/* ------------------------------------------------------------------------
+ * Matching.
+ *
+ * hm_count_matches -- number of matches of p in g (Sec. II-A), computed by
+ * the HiPerMotif hot path (Sec. III-B, III-C): edge scan with the vertex and
+ * edge validators, state injection at depth 2, parallel extension.
+ *   mode   HM_MONO or HM_INDUCED.
+ *   count  HOST uint64 output.
+ * Errors: HM_ERR_ARG, HM_ERR_BUDGET (count invalid; the library stays
+ * usable), HM_ERR_OOM, HM_ERR_CUDA.  Synchronises with its own count copy.
+ * ------------------------------------------------------------------------ */
+hm_status hm_count_matches(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                           uint64_t *count, void *stream);
+
+/* hm_enumerate_matches -- every match as a row of k int32 (original pattern
+ * vertex order), sorted ascending lexicographically, written to rows_dev.
+ *   rows_dev  DEVICE int32[cap * k], owned by the caller (may be NULL if cap == 0).
+ *   cap       rows available.
+ *   count     HOST uint64 output: the number of matches.
+ * If count > cap the call returns HM_ERR_CAPACITY with *count set and the
+ * content of rows_dev unspecified (call again with cap >= *count).  The rows
+ * are complete in stream order on `stream` when the call returns.
+ * Errors as hm_count_matches, plus HM_ERR_CAPACITY. */
+hm_status hm_enumerate_matches(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                               int32_t *rows_dev, uint64_t cap, uint64_t *count, void *stream);
+
+/* hm_count_matches_rooted -- as hm_count_matches, restricted to matches whose
+ * image of ORIGINAL pattern vertex `root` is flagged: root_mask_dev is a DEVICE
+ * uint8[n] (non-zero = allowed).  Used to split a large count into checkable
+ * parts; the union over a partition of V2 is the full count. */
+hm_status hm_count_matches_rooted(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                  int32_t root, const uint8_t *root_mask_dev,
+                                  uint64_t *count, void *stream);
+
+/* hm_injected_states -- the depth-2 states the edge scan produces: every
+ * target arc accepted by the vertex validator (Alg. 2) and the edge
+ * validator (Alg. 3) for the reordered arc between positions 0 and 1, as
+ * pairs (f(pos0), f(pos1)) in unspecified order.
+ *   states_dev DEVICE int32[cap * 2]; count HOST output (total states).
+ * Returns HM_ERR_CAPACITY (with *count) if cap is too small. */
+hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                             int32_t *states_dev, uint64_t cap, uint64_t *count,
+                             void *stream);
+
+/* ------------------------------------------------------------------------
+ * Work budget (watchdog).  Every extension kernel stops when either limit is
+ * reached and the call returns HM_ERR_BUDGET:
+ *   max_ms      wall-clock limit per kernel (0 = default, 120000 ms);
+ *   max_chunks  limit on 32-candidate chunks examined per call (0 = none).
+ * Process-wide setting; takes effect for calls that start afterwards.
+ * ------------------------------------------------------------------------ */
+hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
+
+/* ------------------------------------------------------------------------
+ * Statistics of the calling thread's last matching call (host struct).
+ * When timing is enabled (hm_set_timing(1)), each kernel launch is bracketed
+ * by CUDA events on the call's stream and its duration is reported here.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t seeds_scanned;   /* target arcs scanned by the edge kernel       */
+  uint64_t states_injected; /* depth-2 states after both validators         */
+  uint64_t tasks_donated;   /* work items split off for idle warps          */
+  uint64_t chunks;          /* 32-candidate chunks examined                 */
+  uint64_t matches;         /* the count of the call                        */
+  float ms_edge_scan;       /* edge scan + validators                       */
+  float ms_overlap;         /* neighbour-overlap part of the edge validator  */
+  float ms_extend;          /* persistent extension kernel                  */
+  float ms_sort;            /* row sort (enumerate only)                    */
+  int32_t extend_grid;      /* blocks of the extension launch               */
+  int32_t extend_block;     /* threads per block                            */
+} hm_stats;
+
+hm_status hm_last_stats(hm_stats *out);
+hm_status hm_set_timing(int enabled);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HIPERMOTIF_H */

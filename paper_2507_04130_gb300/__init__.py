@@ -1,0 +1,224 @@
+"""GB300-native labelled subgraph matching with the HiPerMotif method.
+
+Python front end of libhipermotif.so (include/hipermotif.h).  It converts
+numpy arrays / torch tensors to plain pointers and CUDA streams and calls the
+C ABI; PyTorch supplies device memory and streams only.  The library finds
+every match of a small pattern in a large target digraph (Sec. II-A) by
+reordering the pattern (Alg. 1), validating every target arc as the image of
+the pattern's first arc (Alg. 2, Alg. 3), injecting survivors as depth-2
+states and extending them in parallel (Sec. III-C).
+
+    g = Graph(n, src, dst, vlab, elab)          # device-resident target
+    p = Pattern(k, psrc, pdst, pvlab, pelab)    # runs Alg. 1
+    count_matches(g, p, MONO)                   # -> int
+    enumerate_matches(g, p, INDUCED)            # -> torch.int32 [count, k] (cuda)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import binding
+from .binding import HM_INDUCED as INDUCED
+from .binding import HM_MONO as MONO
+from .binding import HMError, check, lib
+
+__all__ = ["Graph", "Pattern", "count_matches", "enumerate_matches", "count_matches_rooted",
+           "injected_states", "set_budget", "set_timing", "last_stats", "MONO", "INDUCED",
+           "HMError", "binding"]
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _host_i32(a) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    if isinstance(a, torch.Tensor):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Graph:
+    """A target graph resident in device memory (CSR + CSC + labels), built on the GPU.
+
+    Arrays may be numpy arrays / CPU tensors (copied from the host) or int32
+    CUDA tensors (read on the device).
+    """
+
+    def __init__(self, n: int, src, dst, vlab, elab, stream=None):
+        arrays = [src, dst, vlab, elab]
+        on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays)
+        if on_dev:
+            keep = [a.to(torch.int32).contiguous() for a in arrays]
+        else:
+            keep = [_host_i32(a) for a in arrays]
+        m = int(keep[0].shape[0])
+        if int(keep[1].shape[0]) != m or int(keep[3].shape[0]) != m or int(keep[2].shape[0]) != n:
+            raise ValueError("array sizes do not match n and m")
+        h = ctypes.c_void_p()
+        st = lib.hm_load_graph(int(n), m, *[_ptr(a) for a in keep], 1 if on_dev else 0,
+                               _stream_ptr(stream), ctypes.byref(h))
+        check(st, "hm_load_graph")
+        self._h = h
+        self.n, self.m = int(n), m
+
+    @classmethod
+    def from_synth(cls, g, stream=None, device: bool = False):
+        if device:
+            t = [torch.from_numpy(np.asarray(a)).cuda() for a in (g.src, g.dst, g.vlab, g.elab)]
+            return cls(g.n, *t, stream=stream)
+        return cls(g.n, g.src, g.dst, g.vlab, g.elab, stream=stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        check(lib.hm_graph_info(self._h, None, None, ctypes.byref(b)), "hm_graph_info")
+        return int(b.value)
+
+    def export(self) -> dict:
+        """Host copies of the built adjacency (offsets int64, lists int32)."""
+        n, m = self.n, self.m
+        out = {k: np.zeros(n + 1, np.int64) for k in ("out_off", "in_off")}
+        out.update({k: np.zeros(max(m, 1), np.int32) for k in ("out_adj", "out_elab", "in_adj", "in_elab")})
+        check(lib.hm_graph_export(self._h, *[_ptr(out[k]) for k in
+                                             ("out_off", "out_adj", "out_elab", "in_off", "in_adj",
+                                              "in_elab")]), "hm_graph_export")
+        for k in ("out_adj", "out_elab", "in_adj", "in_elab"):
+            out[k] = out[k][:m]
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hm_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pattern:
+    """A pattern graph after Alg. 1; host-only (needs no GPU)."""
+
+    def __init__(self, k: int, src, dst, vlab, elab):
+        keep = [_host_i32(a) for a in (src, dst, vlab, elab)]
+        h = ctypes.c_void_p()
+        st = lib.hm_load_pattern(int(k), int(keep[0].shape[0]), *[_ptr(a) for a in keep],
+                                 ctypes.byref(h))
+        check(st, "hm_load_pattern")
+        self._h = h
+        self.k = int(k)
+        self.mp = int(keep[0].shape[0])
+
+    @classmethod
+    def from_synth(cls, p):
+        return cls(p.k, p.src, p.dst, p.vlab, p.elab)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def order(self) -> list[int]:
+        out = np.zeros(self.k, np.int32)
+        check(lib.hm_pattern_order(self._h, _ptr(out)), "hm_pattern_order")
+        return out.tolist()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hm_free_pattern(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def count_matches(g: Graph, p: Pattern, mode: int, stream=None) -> int:
+    c = ctypes.c_uint64()
+    check(lib.hm_count_matches(g.handle, p.handle, int(mode), ctypes.byref(c), _stream_ptr(stream)),
+          "hm_count_matches")
+    return int(c.value)
+
+
+def enumerate_matches(g: Graph, p: Pattern, mode: int, out: torch.Tensor | None = None,
+                      capacity: int | None = None, stream=None) -> torch.Tensor:
+    """All matches as a CUDA int32 tensor [count, k], rows sorted lexicographically.
+
+    `out` (CUDA int32, >= capacity*k elements) is used if given, and a
+    too-small `out` raises HMError(HM_ERR_CAPACITY) carrying the needed count;
+    otherwise a buffer of `capacity` rows (default 1<<20) is allocated, and the
+    call is repeated with the exact size if it was too small.
+    """
+    k = p.k
+    own = out is None
+    if own:
+        cap = int(capacity if capacity is not None else 1 << 20)
+        out = torch.empty(max(cap, 1) * k, dtype=torch.int32, device="cuda")
+    else:
+        cap = int(out.numel() // k) if capacity is None else int(capacity)
+    c = ctypes.c_uint64()
+    st = lib.hm_enumerate_matches(g.handle, p.handle, int(mode), ctypes.c_void_p(out.data_ptr()),
+                                  cap, ctypes.byref(c), _stream_ptr(stream))
+    if st == binding.HM_ERR_CAPACITY and own:
+        need = int(c.value)
+        out = torch.empty(max(need, 1) * k, dtype=torch.int32, device="cuda")
+        st = lib.hm_enumerate_matches(g.handle, p.handle, int(mode), ctypes.c_void_p(out.data_ptr()),
+                                      need, ctypes.byref(c), _stream_ptr(stream))
+    check(st, "hm_enumerate_matches", int(c.value))
+    return out[: int(c.value) * k].view(int(c.value), k)
+
+
+def count_matches_rooted(g: Graph, p: Pattern, mode: int, root: int, mask, stream=None) -> int:
+    """Count only matches whose image of original pattern vertex `root` is flagged in mask (uint8[n])."""
+    if not (isinstance(mask, torch.Tensor) and mask.is_cuda):
+        mask = torch.as_tensor(np.asarray(mask, dtype=np.uint8)).cuda()
+    mask = mask.to(torch.uint8).contiguous()
+    c = ctypes.c_uint64()
+    check(lib.hm_count_matches_rooted(g.handle, p.handle, int(mode), int(root),
+                                      ctypes.c_void_p(mask.data_ptr()), ctypes.byref(c),
+                                      _stream_ptr(stream)), "hm_count_matches_rooted")
+    return int(c.value)
+
+
+def injected_states(g: Graph, p: Pattern, mode: int, stream=None) -> torch.Tensor:
+    """The depth-2 states after both validators, as a CUDA int32 tensor [S, 2] (unordered)."""
+    cap = max(g.m, 1)
+    out = torch.empty(cap * 2, dtype=torch.int32, device="cuda")
+    c = ctypes.c_uint64()
+    check(lib.hm_injected_states(g.handle, p.handle, int(mode), ctypes.c_void_p(out.data_ptr()), cap,
+                                 ctypes.byref(c), _stream_ptr(stream)), "hm_injected_states")
+    return out[: int(c.value) * 2].view(int(c.value), 2)
+
+
+def set_budget(max_ms: int = 0, max_chunks: int = 0):
+    check(lib.hm_set_budget(int(max_ms), int(max_chunks)), "hm_set_budget")
+
+
+def set_timing(enabled: bool):
+    check(lib.hm_set_timing(1 if enabled else 0), "hm_set_timing")
+
+
+def last_stats() -> dict:
+    s = binding.hm_stats()
+    check(lib.hm_last_stats(ctypes.byref(s)), "hm_last_stats")
+    return s.as_dict()

@@ -1,0 +1,104 @@
+"""ctypes binding of libhipermotif.so: the C ABI of include/hipermotif.h, same names.
+
+Argument marshalling only -- every step of the matching path runs in the CUDA
+library.  Importing this module loads the library and raises ImportError if
+it has not been built (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+HM_OK, HM_ERR_ARG, HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_PATTERN = 0, 1, 2, 3, 4
+HM_ERR_OOM, HM_ERR_CAPACITY, HM_ERR_BUDGET, HM_ERR_CUDA, HM_ERR_NO_DEVICE = 5, 6, 7, 8, 9
+HM_MONO, HM_INDUCED = 0, 1
+HM_MAX_K = 16
+
+#: every function include/hipermotif.h declares
+EXPORTED = [
+    "hm_status_str", "hm_load_graph", "hm_free_graph", "hm_graph_info", "hm_graph_export",
+    "hm_graph_export_groups",
+    "hm_load_pattern", "hm_free_pattern", "hm_pattern_order", "hm_count_matches",
+    "hm_enumerate_matches", "hm_count_matches_rooted", "hm_injected_states", "hm_set_budget",
+    "hm_last_stats", "hm_set_timing",
+]
+
+
+class hm_stats(ctypes.Structure):
+    _fields_ = [
+        ("seeds_scanned", ctypes.c_uint64),
+        ("states_injected", ctypes.c_uint64),
+        ("tasks_donated", ctypes.c_uint64),
+        ("chunks", ctypes.c_uint64),
+        ("matches", ctypes.c_uint64),
+        ("ms_edge_scan", ctypes.c_float),
+        ("ms_overlap", ctypes.c_float),
+        ("ms_extend", ctypes.c_float),
+        ("ms_sort", ctypes.c_float),
+        ("extend_grid", ctypes.c_int32),
+        ("extend_block", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_st = ctypes.c_int
+_pvp = ctypes.POINTER(ctypes.c_void_p)
+_pu64 = ctypes.POINTER(ctypes.c_uint64)
+
+_SIGS = {
+    "hm_status_str": (ctypes.c_char_p, [_st]),
+    "hm_load_graph": (_st, [_i32, _i64, _vp, _vp, _vp, _vp, ctypes.c_int, _vp, _pvp]),
+    "hm_free_graph": (None, [_vp]),
+    "hm_graph_info": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64),
+                            ctypes.POINTER(ctypes.c_size_t)]),
+    "hm_graph_export": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hm_graph_export_groups": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hm_load_pattern": (_st, [_i32, _i32, _vp, _vp, _vp, _vp, _pvp]),
+    "hm_free_pattern": (None, [_vp]),
+    "hm_pattern_order": (_st, [_vp, _vp]),
+    "hm_count_matches": (_st, [_vp, _vp, ctypes.c_int, _pu64, _vp]),
+    "hm_enumerate_matches": (_st, [_vp, _vp, ctypes.c_int, _vp, _u64, _pu64, _vp]),
+    "hm_count_matches_rooted": (_st, [_vp, _vp, ctypes.c_int, _i32, _vp, _pu64, _vp]),
+    "hm_injected_states": (_st, [_vp, _vp, ctypes.c_int, _vp, _u64, _pu64, _vp]),
+    "hm_set_budget": (_st, [_u64, _u64]),
+    "hm_last_stats": (_st, [ctypes.POINTER(hm_stats)]),
+    "hm_set_timing": (_st, [ctypes.c_int]),
+}
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class HMError(RuntimeError):
+    def __init__(self, status: int, where: str, count: int | None = None):
+        self.status = int(status)
+        self.count = count
+        msg = lib.hm_status_str(self.status).decode()
+        super().__init__(f"{where}: {msg} (status {self.status})")
+
+
+def check(status: int, where: str, count: int | None = None):
+    if status != HM_OK:
+        raise HMError(status, where, count)

@@ -1,0 +1,196 @@
+// hm_internal.cuh -- types and device helpers shared by the library's sources.
+//
+// Layout of a loaded target graph in HBM (all arrays 256-byte aligned):
+//   src      int32[m]  source of each arc, CSR order (the per-arc source array
+//                      of the double-index storage, Sec. III-D)
+//   out_adj  int32[m]  out-neighbours, sorted within each vertex
+//   out_elab int32[m]  label of each out-arc, parallel to out_adj
+//   in_adj   int32[m]  in-neighbours, sorted within each vertex (CSC)
+//   in_elab  int32[m]  label of each in-arc, parallel to in_adj
+//   vi       int4[n]   {vertex label, out-degree, in-degree, 0}
+//   off      longlong2[n] {first out-arc, first in-arc}
+// A vertex's label and both degrees arrive in one 16-byte load; its list
+// offsets in a second one, fetched only when a list is actually searched.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hipermotif.h"
+
+namespace hm {
+
+constexpr int kMaxK = HM_MAX_K;
+constexpr int kMaxCons = 2 * (HM_MAX_K - 1);
+constexpr int kWarp = 32;
+
+struct DevGraph {
+  int32_t n;
+  int64_t m;
+  const int32_t *src;
+  const int32_t *out_adj;
+  const int32_t *out_elab;
+  const int32_t *in_adj;
+  const int32_t *in_elab;
+  const int4 *vi;
+  const longlong2 *off;
+  // label-grouped copies of the lists: each vertex's list ordered by
+  // (arc label, neighbour label, neighbour id); one directory entry per group
+  const int32_t *gout_adj;
+  const int32_t *gin_adj;
+  const int4 *gdir_out;  // {arc label, neighbour label, first, end} (relative to the list start)
+  const int4 *gdir_in;
+  const int4 *vdir;      // {first out entry, out entries, first in entry, in entries}
+};
+
+// One pairwise condition between the position being extended (p) and an
+// earlier position q, on the candidate c for p:
+enum ConsKind : int8_t {
+  kOut = 0,     // arc f(q) -> c must exist with label `lab`   (pattern arc q->p)
+  kIn = 1,      // arc c -> f(q) must exist with label `lab`   (pattern arc p->q)
+  kNotOut = 2,  // no arc f(q) -> c                            (induced, non-arc q->p)
+  kNotIn = 3,   // no arc c -> f(q)                            (induced, non-arc p->q)
+};
+
+struct Cons {
+  int8_t q;
+  int8_t kind;
+  int16_t pad;
+  int32_t lab;
+};
+
+// Per-pattern, per-mode plan, indexed by position after Alg. 1.
+struct Plan {
+  int32_t k;
+  int32_t induced;
+  int32_t orig[kMaxK];  // position -> original pattern vertex
+  int32_t vlab[kMaxK];  // label required at each position
+  int32_t din[kMaxK];   // pattern in-degree at each position
+  int32_t dout[kMaxK];  // pattern out-degree at each position
+  // the seeding arc between positions 0 and 1
+  int32_t seed_rev;     // 0: target arc (a,b) gives f(0)=a, f(1)=b; 1: f(0)=b, f(1)=a
+  int32_t seed_lab;     // label of that pattern arc
+  int32_t back_req;     // pattern also has 1->0: target arc f(1)->f(0) needed, label back_lab
+  int32_t back_lab;
+  int32_t back_forbid;  // induced, and the pattern lacks the opposite arc: forbid it in the target
+  int32_t ov_need;      // |N(0) & N(1)| in the pattern (neighbour-overlap test)
+  int32_t root_pos;     // position whose image must pass a root mask, or -1
+  int32_t ncons[kMaxK]; // conditions for position p (positives first)
+  int32_t npos[kMaxK];  // how many of them are kOut/kIn
+  int32_t gbase[kMaxK]; // first group slot of position p (sum of npos before p)
+  int32_t ngrp;         // group slots in total
+  Cons cons[kMaxK][kMaxCons];
+};
+
+// Budget / status words shared by all warps of one call.
+enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+// First index i in the sorted list a[lo, lo+len) with a[i] >= x (lo+len if none).
+__device__ __forceinline__ int64_t lower_bound_idx(const int32_t *__restrict__ a, int64_t lo,
+                                                   int64_t len, int32_t x) {
+  while (len > 0) {
+    int64_t half = len >> 1;
+    int32_t v = __ldg(a + lo + half);
+    if (v < x) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo;
+}
+
+// Is x in a[lo, lo+len)?  Returns its index or -1.
+__device__ __forceinline__ int64_t search(const int32_t *__restrict__ a, int64_t lo, int64_t len,
+                                          int32_t x) {
+  int64_t end = lo + len;
+  int64_t i = lower_bound_idx(a, lo, len, x);
+  return (i < end && __ldg(a + i) == x) ? i : -1;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+#endif  // __CUDACC__
+
+}  // namespace hm
+
+// ---------------------------------------------------------------------------
+// host-side objects
+// ---------------------------------------------------------------------------
+
+struct hm_graph {
+  int device;
+  int32_t n;
+  int64_t m;
+  int32_t *src, *out_adj, *out_elab, *in_adj, *in_elab;
+  int4 *vi;
+  longlong2 *off;
+  int32_t *gout_adj, *gin_adj;
+  int4 *gdir_out, *gdir_in, *vdir;
+  int64_t ndir_out, ndir_in;
+  size_t bytes;
+  hm::DevGraph dev() const {
+    return hm::DevGraph{n,        m,       src,      out_adj,  out_elab, in_adj, in_elab, vi,
+                        off,      gout_adj, gin_adj, gdir_out, gdir_in,  vdir};
+  }
+};
+
+struct hm_pattern {
+  int32_t k, mp;
+  int32_t order[HM_MAX_K];
+  hm::Plan plan[2];  // [mode]
+};
+
+namespace hm {
+
+// Thread-local record of the last call (hm_last_stats).
+hm_stats &tls_stats();
+bool timing_enabled();
+uint64_t budget_ms();
+uint64_t budget_chunks();
+
+// Sort rows of `width` int32 words lexicographically by the `nkey` columns
+// listed in key_cols (most significant first); every key value must lie in
+// [0, 2^bits).  `rows` and `tmp` hold nrows*width words each; the sorted rows
+// end in `rows`.  Stable.  Launches on `stream`.
+hm_status radix_sort_rows(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
+                          const int *key_cols, int nkey, int bits, cudaStream_t stream);
+
+// As radix_sort_rows, with a bit width (1..32) and an xor mask per key column
+// (the xor maps signed values to an unsigned order, e.g. 0x80000000).
+hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
+                               const int *key_cols, const int *key_bits, const uint32_t *key_xor,
+                               int nkey, cudaStream_t stream);
+
+// out[i] = in[0] + ... + in[i-1] for i in [0, n); values and total below 2^32.
+hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t stream);
+
+int bits_for(int64_t n);  // bits needed for values in [0, n)
+int num_sms();
+
+}  // namespace hm
+
+#define HM_CUDA_TRY(expr)                                    \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) {                                 \
+      (void)cudaGetLastError();                              \
+      return e_ == cudaErrorMemoryAllocation ? HM_ERR_OOM    \
+                                             : HM_ERR_CUDA;  \
+    }                                                        \
+  } while (0)

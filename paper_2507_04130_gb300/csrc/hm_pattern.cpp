@@ -1,0 +1,209 @@
+// hm_pattern.cpp -- pattern validation, Structural Reordering (Alg. 1) and the
+// per-position plans the kernels run (host code; needs no GPU).
+//
+// Alg. 1 (Sec. III-A): rank sigma(v) = (totaldeg(v), outdeg(v)) compared
+// lexicographically; the sigma-argmax goes to position 0; then, while vertices
+// remain, the next position takes the sigma-argmax among the unplaced
+// out-neighbours of the vertex placed last, or among all unplaced vertices if
+// it has none.  Readings where the paper is silent or garbled:
+//   * ties beyond outdeg go to the lowest original id;
+//   * degrees are the pattern's static degrees (nothing is re-ranked);
+//   * positions are 0-based (the listing's 1-based pi(1) is position 0);
+//   * if the fallback pick has no arc to any placed vertex, the sigma-argmax
+//     among unplaced vertices that do have one is taken instead, so every
+//     position >= 1 has at least one arc to an earlier position (an anchor).
+//
+// Plan (what the kernels check at each position, Sec. III-B/C):
+//   positions 0,1 -- the seeding arc: normally pattern arc 0->1, so a target
+//     arc (a,b) proposes f(0)=a, f(1)=b; if the pattern only has 1->0, the
+//     target arc (a,b) proposes f(1)=a, f(0)=b.  The edge validator's other
+//     direction: required with its label when the pattern has both arcs,
+//     forbidden in induced mode when the pattern has only one.
+//   position p >= 2 -- for every earlier q: the pattern arcs between q and p
+//     become "arc must exist with this label" conditions, and in induced mode
+//     the missing ones become "arc must not exist" conditions.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "hm_internal.cuh"
+
+namespace {
+
+struct PatternGraph {
+  int k = 0;
+  bool arc[HM_MAX_K][HM_MAX_K] = {};
+  int32_t lab[HM_MAX_K][HM_MAX_K] = {};
+  int32_t vlab[HM_MAX_K] = {};
+  int indeg[HM_MAX_K] = {};
+  int outdeg[HM_MAX_K] = {};
+};
+
+bool sigma_less(const PatternGraph &P, int a, int b) {
+  int ta = P.indeg[a] + P.outdeg[a], tb = P.indeg[b] + P.outdeg[b];
+  if (ta != tb) return ta < tb;
+  return P.outdeg[a] < P.outdeg[b];
+}
+
+// sigma-argmax over the vertices flagged in `cand` (lowest id wins ties); -1 if none.
+int argmax_sigma(const PatternGraph &P, const bool *cand) {
+  int best = -1;
+  for (int v = 0; v < P.k; ++v) {
+    if (!cand[v]) continue;
+    if (best < 0 || sigma_less(P, best, v)) best = v;
+  }
+  return best;
+}
+
+void structural_reorder(const PatternGraph &P, int32_t *order) {
+  bool placed[HM_MAX_K] = {};
+  bool cand[HM_MAX_K];
+  for (int v = 0; v < P.k; ++v) cand[v] = true;
+  int n_placed = 0;
+  order[n_placed] = argmax_sigma(P, cand);
+  placed[order[n_placed++]] = true;
+  while (n_placed < P.k) {
+    int u = order[n_placed - 1];
+    bool any = false;
+    for (int w = 0; w < P.k; ++w) {
+      cand[w] = !placed[w] && P.arc[u][w];
+      any |= cand[w];
+    }
+    int w_star;
+    if (any) {
+      w_star = argmax_sigma(P, cand);
+    } else {
+      for (int w = 0; w < P.k; ++w) cand[w] = !placed[w];
+      w_star = argmax_sigma(P, cand);
+      bool anchored = false;
+      for (int r = 0; r < P.k; ++r)
+        if (placed[r] && (P.arc[w_star][r] || P.arc[r][w_star])) anchored = true;
+      if (!anchored) {
+        bool found = false;
+        for (int w = 0; w < P.k; ++w) {
+          cand[w] = false;
+          if (placed[w]) continue;
+          for (int r = 0; r < P.k; ++r)
+            if (placed[r] && (P.arc[w][r] || P.arc[r][w])) cand[w] = true;
+          found |= cand[w];
+        }
+        if (found) w_star = argmax_sigma(P, cand);
+      }
+    }
+    order[n_placed++] = w_star;
+    placed[w_star] = true;
+  }
+}
+
+void build_plan(const PatternGraph &P, const int32_t *order, int induced, hm::Plan &pl) {
+  std::memset(&pl, 0, sizeof(pl));
+  const int k = P.k;
+  pl.k = k;
+  pl.induced = induced;
+  pl.root_pos = -1;
+  bool A[HM_MAX_K][HM_MAX_K];
+  int32_t L[HM_MAX_K][HM_MAX_K];
+  for (int i = 0; i < k; ++i) {
+    pl.orig[i] = order[i];
+    pl.vlab[i] = P.vlab[order[i]];
+    pl.din[i] = P.indeg[order[i]];
+    pl.dout[i] = P.outdeg[order[i]];
+    for (int j = 0; j < k; ++j) {
+      A[i][j] = P.arc[order[i]][order[j]];
+      L[i][j] = P.lab[order[i]][order[j]];
+    }
+  }
+  if (A[0][1]) {
+    pl.seed_rev = 0;
+    pl.seed_lab = L[0][1];
+    pl.back_req = A[1][0] ? 1 : 0;
+    pl.back_lab = A[1][0] ? L[1][0] : 0;
+    pl.back_forbid = (induced && !A[1][0]) ? 1 : 0;
+  } else {
+    pl.seed_rev = 1;
+    pl.seed_lab = L[1][0];
+    pl.back_req = 0;
+    pl.back_lab = 0;
+    pl.back_forbid = induced ? 1 : 0;
+  }
+  int ov = 0;
+  for (int w = 2; w < k; ++w)
+    if ((A[0][w] || A[w][0]) && (A[1][w] || A[w][1])) ++ov;
+  pl.ov_need = ov;
+  int slots = 0;
+  for (int p = 2; p < k; ++p) {
+    int c = 0;
+    pl.gbase[p] = slots;
+    for (int q = 0; q < p; ++q) {
+      if (A[q][p]) pl.cons[p][c++] = hm::Cons{(int8_t)q, hm::kOut, 0, L[q][p]};
+      if (A[p][q]) pl.cons[p][c++] = hm::Cons{(int8_t)q, hm::kIn, 0, L[p][q]};
+    }
+    pl.npos[p] = c;
+    slots += c;
+    if (induced) {
+      for (int q = 0; q < p; ++q) {
+        if (!A[q][p]) pl.cons[p][c++] = hm::Cons{(int8_t)q, hm::kNotOut, 0, 0};
+        if (!A[p][q]) pl.cons[p][c++] = hm::Cons{(int8_t)q, hm::kNotIn, 0, 0};
+      }
+    }
+    pl.ncons[p] = c;
+  }
+  pl.ngrp = slots;
+}
+
+bool weakly_connected(const PatternGraph &P) {
+  int parent[HM_MAX_K];
+  for (int i = 0; i < P.k; ++i) parent[i] = i;
+  auto find = [&](int x) {
+    while (parent[x] != x) x = parent[x] = parent[parent[x]];
+    return x;
+  };
+  for (int a = 0; a < P.k; ++a)
+    for (int b = 0; b < P.k; ++b)
+      if (P.arc[a][b]) parent[find(a)] = find(b);
+  int root = find(0);
+  for (int i = 1; i < P.k; ++i)
+    if (find(i) != root) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" hm_status hm_load_pattern(int32_t k, int32_t mp, const int32_t *src,
+                                     const int32_t *dst, const int32_t *vlab,
+                                     const int32_t *elab, hm_pattern **out) {
+  if (!out || !vlab || mp < 0) return HM_ERR_ARG;
+  if (k < 2 || k > HM_MAX_K || mp < 1) return HM_ERR_PATTERN;
+  if (!src || !dst || !elab) return HM_ERR_ARG;
+  PatternGraph P;
+  P.k = k;
+  for (int i = 0; i < k; ++i) P.vlab[i] = vlab[i];
+  for (int e = 0; e < mp; ++e) {
+    int a = src[e], b = dst[e];
+    if (a < 0 || a >= k || b < 0 || b >= k) return HM_ERR_ARG;
+    if (a == b) return HM_ERR_SELF_LOOP;
+    if (P.arc[a][b]) return HM_ERR_DUP_EDGE;
+    P.arc[a][b] = true;
+    P.lab[a][b] = elab[e];
+    P.outdeg[a]++;
+    P.indeg[b]++;
+  }
+  if (!weakly_connected(P)) return HM_ERR_PATTERN;
+  hm_pattern *p = new (std::nothrow) hm_pattern();
+  if (!p) return HM_ERR_OOM;
+  p->k = k;
+  p->mp = mp;
+  structural_reorder(P, p->order);
+  build_plan(P, p->order, 0, p->plan[0]);
+  build_plan(P, p->order, 1, p->plan[1]);
+  *out = p;
+  return HM_OK;
+}
+
+extern "C" void hm_free_pattern(hm_pattern *p) { delete p; }
+
+extern "C" hm_status hm_pattern_order(const hm_pattern *p, int32_t *order_out) {
+  if (!p || !order_out) return HM_ERR_ARG;
+  for (int i = 0; i < p->k; ++i) order_out[i] = p->order[i];
+  return HM_OK;
+}

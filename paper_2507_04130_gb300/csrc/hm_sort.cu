@@ -1,0 +1,357 @@
+// hm_sort.cu -- stable least-significant-digit radix sort of fixed-width int32 rows.
+//
+// Used twice on the path: to put the target's arcs in (src, dst) and (dst, src)
+// order when a graph is loaded, and to put the output mappings in
+// lexicographic order (original pattern-vertex columns) before they are
+// returned.  The key is the concatenation of the chosen columns, each
+// holding `bits` significant bits, most significant column first; it is
+// consumed 8 bits per pass.
+//
+// One pass = three kernels on a fixed grid of G blocks, block b owning the
+// contiguous row range [b*R, (b+1)*R):
+//   k_hist     per-block digit histogram          -> hist[digit * G + b]
+//   k_scan     exclusive scan of hist (one block)  -> global start of each
+//              (digit, block) bucket
+//   k_scatter  the block walks its range in tiles of 1024 rows; inside a
+//              tile each warp ranks its 4 rounds of 32 rows with
+//              __match_any_sync, warps are ordered by an exclusive prefix over
+//              their per-digit counts, so equal digits keep input order
+//              (stability), and rows are copied to their final slots.
+#include <algorithm>
+
+#include "hm_internal.cuh"
+
+namespace hm {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kItems = 4;
+constexpr int kTile = kSortThreads * kItems;
+constexpr int kMaxKeyCols = 16;
+
+struct KeySpec {
+  int ncols;                 // key columns
+  int cols[kMaxKeyCols];     // row word of each key column, most significant first
+  int bits[kMaxKeyCols];     // significant bits of each key column (1..32)
+  uint32_t xr[kMaxKeyCols];  // xor applied to a column before its bits are taken
+  int shift;                 // bit position of this pass's digit within the whole key
+};
+
+// 8-bit digit starting at bit `shift` of the concatenated key of a row.
+__device__ __forceinline__ uint32_t digit_of(const int32_t *__restrict__ row, const KeySpec &ks) {
+  uint32_t v = 0;
+  int got = 0;
+  int col_lo = 0;  // bit position of the current column's least significant bit
+  for (int i = ks.ncols - 1; i >= 0 && got < 8; --i) {
+    const int b = ks.bits[i];
+    const int want_lo = ks.shift + got;
+    if (want_lo < col_lo + b) {
+      const int r = want_lo - col_lo;
+      const int take = min(b - r, 8 - got);
+      const uint32_t col = (uint32_t)__ldg(row + ks.cols[i]) ^ ks.xr[i];
+      v |= ((col >> r) & ((take >= 32) ? 0xffffffffu : ((1u << take) - 1u))) << got;
+      got += take;
+    }
+    col_lo += b;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_hist(const int32_t *__restrict__ rows, int64_t nrows, int width, int64_t per_block,
+       KeySpec ks, uint32_t *__restrict__ hist, int grid) {
+  __shared__ uint32_t h[kRadix];
+  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  int64_t lo = (int64_t)blockIdx.x * per_block;
+  int64_t hi = min(nrows, lo + per_block);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    atomicAdd(&h[digit_of(rows + i * width, ks)], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * grid + blockIdx.x] = h[d];
+}
+
+// Exclusive scan of `len` uint32 values in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan(uint32_t *__restrict__ a, int64_t len) {
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < len; base += 1024) {
+    int64_t i = base + threadIdx.x;
+    uint32_t v = i < len ? a[i] : 0;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t s = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t before = carry + (warp ? warp_sums[warp - 1] : 0) + x - v;
+    if (i < len) a[i] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sums[31];
+    __syncthreads();
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kSortThreads)
+k_scatter(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nrows,
+          int64_t per_block, KeySpec ks, const uint32_t *__restrict__ starts, int grid) {
+  __shared__ uint32_t s_base[kRadix];
+  __shared__ uint32_t s_cnt[kSortWarps][kRadix];
+  __shared__ uint32_t s_tile[kRadix];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    s_base[d] = starts[(int64_t)d * grid + blockIdx.x];
+  int64_t lo = (int64_t)blockIdx.x * per_block;
+  int64_t hi = min(nrows, lo + per_block);
+  const uint32_t lt = lanemask_lt();
+  for (int64_t tile = lo; tile < hi; tile += kTile) {
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t dig[kItems], rank[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      int64_t i = tile + (int64_t)warp * 32 * kItems + r * 32 + lane;
+      bool valid = i < hi;
+      uint32_t d = valid ? digit_of(in + i * W, ks) : kRadix;
+      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      int leader = __ffs(peers) - 1;
+      uint32_t prev = 0;
+      if (valid && lane == leader) {
+        prev = s_cnt[warp][d];
+        s_cnt[warp][d] = prev + __popc(peers);
+      }
+      prev = __shfl_sync(0xffffffffu, prev, leader);
+      dig[r] = d;
+      rank[r] = prev + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {
+        uint32_t t = s_cnt[w][d];
+        s_cnt[w][d] = acc;
+        acc += t;
+      }
+      s_tile[d] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      int64_t i = tile + (int64_t)warp * 32 * kItems + r * 32 + lane;
+      if (i < hi) {
+        uint32_t d = dig[r];
+        int64_t pos = (int64_t)s_base[d] + s_cnt[warp][d] + rank[r];
+        const int32_t *src = in + i * W;
+        int32_t *dst = out + pos * W;
+#pragma unroll
+        for (int w = 0; w < W; ++w) dst[w] = src[w];
+      }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) s_base[d] += s_tile[d];
+    __syncthreads();
+  }
+}
+
+template <int W>
+void launch_scatter(const int32_t *in, int32_t *out, int64_t nrows, int64_t per_block, KeySpec ks,
+                    const uint32_t *starts, int grid, cudaStream_t s) {
+  k_scatter<W><<<grid, kSortThreads, 0, s>>>(in, out, nrows, per_block, ks, starts, grid);
+}
+
+using ScatterFn = void (*)(const int32_t *, int32_t *, int64_t, int64_t, KeySpec,
+                           const uint32_t *, int, cudaStream_t);
+
+ScatterFn scatter_for(int width) {
+  switch (width) {
+    case 1: return launch_scatter<1>;
+    case 2: return launch_scatter<2>;
+    case 3: return launch_scatter<3>;
+    case 4: return launch_scatter<4>;
+    case 5: return launch_scatter<5>;
+    case 6: return launch_scatter<6>;
+    case 7: return launch_scatter<7>;
+    case 8: return launch_scatter<8>;
+    case 9: return launch_scatter<9>;
+    case 10: return launch_scatter<10>;
+    case 11: return launch_scatter<11>;
+    case 12: return launch_scatter<12>;
+    case 13: return launch_scatter<13>;
+    case 14: return launch_scatter<14>;
+    case 15: return launch_scatter<15>;
+    case 16: return launch_scatter<16>;
+    default: return nullptr;
+  }
+}
+
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < kScanThreads / 32 ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) ws[lane] = s;
+  }
+  __syncthreads();
+  uint32_t before = (warp ? ws[warp - 1] : 0) + x - v;
+  *total = ws[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_tile_sums(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += in[base + i];
+  uint32_t total;
+  block_excl_scan(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_tile_scan(const uint32_t *__restrict__ in, int64_t n, const uint32_t *__restrict__ offs,
+            uint32_t *__restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0;
+    s += v[i];
+  }
+  uint32_t total;
+  uint32_t run = block_excl_scan(s, &total) + offs[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+}  // namespace
+
+hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return HM_OK;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  uint32_t *sums = nullptr;
+  HM_CUDA_TRY(cudaMallocAsync(&sums, sizeof(uint32_t) * (size_t)tiles, s));
+  k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+  k_scan<<<1, 1024, 0, s>>>(sums, tiles);
+  k_tile_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums, out);
+  HM_CUDA_TRY(cudaFreeAsync(sums, s));
+  HM_CUDA_TRY(cudaGetLastError());
+  return HM_OK;
+}
+
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 31 && (int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 1;
+    cached = v;
+  }
+  return cached;
+}
+
+hm_status radix_sort_rows(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
+                          const int *key_cols, int nkey, int bits, cudaStream_t stream) {
+  int b[kMaxKeyCols];
+  uint32_t x[kMaxKeyCols];
+  if (nkey < 1 || nkey > kMaxKeyCols) return HM_ERR_ARG;
+  for (int i = 0; i < nkey; ++i) {
+    b[i] = bits;
+    x[i] = 0;
+  }
+  return radix_sort_rows_cols(rows, tmp, nrows, width, key_cols, b, x, nkey, stream);
+}
+
+hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
+                               const int *key_cols, const int *key_bits, const uint32_t *key_xor,
+                               int nkey, cudaStream_t stream) {
+  if (nrows <= 1) return HM_OK;
+  ScatterFn scatter = scatter_for(width);
+  if (!scatter || nkey < 1 || nkey > kMaxKeyCols) return HM_ERR_ARG;
+  KeySpec ks{};
+  ks.ncols = nkey;
+  int total_bits = 0;
+  for (int i = 0; i < nkey; ++i) {
+    if (key_bits[i] < 1 || key_bits[i] > 32 || key_cols[i] < 0 || key_cols[i] >= width)
+      return HM_ERR_ARG;
+    ks.cols[i] = key_cols[i];
+    ks.bits[i] = key_bits[i];
+    ks.xr[i] = key_xor[i];
+    total_bits += key_bits[i];
+  }
+  const int passes = (total_bits + 7) / 8;
+  int grid = (int)std::min<int64_t>((nrows + kTile - 1) / kTile, (int64_t)num_sms() * 4);
+  int64_t per_block = (nrows + grid - 1) / grid;
+  per_block = (per_block + kTile - 1) / kTile * kTile;
+  grid = (int)((nrows + per_block - 1) / per_block);
+  uint32_t *hist = nullptr;
+  HM_CUDA_TRY(cudaMallocAsync(&hist, sizeof(uint32_t) * kRadix * grid, stream));
+  int32_t *a = rows, *b = tmp;
+  for (int p = 0; p < passes; ++p) {
+    ks.shift = p * 8;
+    k_hist<<<grid, kSortThreads, 0, stream>>>(a, nrows, width, per_block, ks, hist, grid);
+    k_scan<<<1, 1024, 0, stream>>>(hist, (int64_t)kRadix * grid);
+    scatter(a, b, nrows, per_block, ks, hist, grid, stream);
+    std::swap(a, b);
+  }
+  if (a != rows)
+    HM_CUDA_TRY(cudaMemcpyAsync(rows, a, sizeof(int32_t) * nrows * width,
+                                cudaMemcpyDeviceToDevice, stream));
+  HM_CUDA_TRY(cudaFreeAsync(hist, stream));
+  HM_CUDA_TRY(cudaGetLastError());
+  return HM_OK;
+}
+
+}  // namespace hm

@@ -1,0 +1,104 @@
+"""Host-side tests of the C ABI that need no GPU.
+
+  * the library loads and exports every function include/hipermotif.h declares;
+  * hm_load_pattern validates patterns and runs Alg. 1 exactly like the
+    oracle's plain restatement (hand-worked cases and random patterns);
+  * loading a graph without a device fails with a status, not a crash.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import steps
+from tests import _golden
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2507_04130_gb300 as mod
+    return mod
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "hipermotif.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hm_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(hm):
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(hm.lib, name), name
+    assert sorted(hm.binding.EXPORTED) == declared
+
+
+def test_status_strings(hm):
+    for s in range(10):
+        assert hm.lib.hm_status_str(s)
+    assert hm.lib.hm_status_str(hm.binding.HM_ERR_CAPACITY).decode() == "output capacity too small"
+
+
+@pytest.mark.parametrize("case", _golden.reorder_cases(), ids=lambda c: c["name"])
+def test_pattern_order_hand_worked(hm, case):
+    src = [a for a, _ in case["arcs"]]
+    dst = [b for _, b in case["arcs"]]
+    p = hm.Pattern(case["k"], src, dst, [0] * case["k"], [0] * len(src))
+    assert p.order == case["order"]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_pattern_order_equals_plain_alg1(hm, seed):
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(2, 17))
+    p = synth.random_pattern(rng, k, float(rng.uniform(0.05, 0.8)), n_vlab=2, n_elab=2)
+    assert hm.Pattern.from_synth(p).order == steps.structural_reorder(k, p.src, p.dst)
+
+
+def test_config_patterns_order(hm):
+    for p in synth.config2_patterns() + synth.config3_patterns() + synth.config4_patterns(count=32):
+        assert hm.Pattern.from_synth(p).order == steps.structural_reorder(p.k, p.src, p.dst)
+
+
+@pytest.mark.parametrize("k,src,dst,status", [
+    (1, [0], [0], "HM_ERR_PATTERN"),                       # k < 2
+    (17, [0], [1], "HM_ERR_PATTERN"),                      # k > 16
+    (3, [], [], "HM_ERR_PATTERN"),                         # no arc
+    (3, [0, 1], [0, 2], "HM_ERR_SELF_LOOP"),
+    (3, [0, 0], [1, 1], "HM_ERR_DUP_EDGE"),
+    (4, [0, 2], [1, 3], "HM_ERR_PATTERN"),                 # not weakly connected
+    (3, [0, 1], [1, 5], "HM_ERR_ARG"),                     # id out of range
+])
+def test_pattern_validation(hm, k, src, dst, status):
+    with pytest.raises(hm.HMError) as ei:
+        hm.Pattern(k, src, dst, [0] * max(k, 1), [0] * len(src))
+    assert ei.value.status == getattr(hm.binding, status)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")
+def test_graph_load_without_device_reports_status(hm):
+    arrs = [np.array(a, np.int32) for a in ([0, 1], [1, 2], [0, 0, 0], [0, 0])]
+    h = ctypes.c_void_p()
+    st = hm.lib.hm_load_graph(3, 2, *[ctypes.c_void_p(a.ctypes.data) for a in arrs], 0, None,
+                              ctypes.byref(h))
+    assert st in (hm.binding.HM_ERR_NO_DEVICE, hm.binding.HM_ERR_CUDA)
+
+
+def test_graph_load_rejects_bad_arguments_before_the_device(hm):
+    h = ctypes.c_void_p()
+    assert hm.lib.hm_load_graph(-1, 0, None, None, None, None, 0, None, ctypes.byref(h)) == \
+        hm.binding.HM_ERR_ARG
+    assert hm.lib.hm_load_graph(3, 2, None, None, None, None, 0, None, ctypes.byref(h)) == \
+        hm.binding.HM_ERR_ARG

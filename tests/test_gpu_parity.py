@@ -1,0 +1,336 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit-exact (integer work).
+
+Counts and the sorted row lists must be identical; the intermediate results
+(built adjacency, injected depth-2 states) are checked against plain
+restatements (numpy sort, oracle/steps.py).  All calls go through the C ABI.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import steps
+from tests import _golden
+
+pytestmark = pytest.mark.gpu
+
+MODES = (oracle.MONO, oracle.INDUCED)
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2507_04130_gb300 as mod
+    assert torch.cuda.is_available()
+    mod.set_budget(60_000, 0)
+    return mod
+
+
+def _check(hm, G, og, sp, mode, rows=True):
+    P = hm.Pattern.from_synth(sp)
+    want_count, want_rows = og.match(sp, mode, rows=rows)
+    got = hm.count_matches(G, P, mode)
+    assert got == want_count, (sp.name, mode, got, want_count)
+    if rows:
+        r = hm.enumerate_matches(G, P, mode).cpu().numpy()
+        assert r.shape == want_rows.shape
+        np.testing.assert_array_equal(r, want_rows)
+    return want_count
+
+
+# ---------------------------------------------------------------------------
+# graph build
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(4))
+def test_graph_build_matches_numpy_sort(hm, seed):
+    g = synth.er_graph(3000 + 517 * seed, 40000 + 999 * seed, 4, 5, seed=seed)
+    for device in (False, True):
+        G = hm.Graph.from_synth(g, device=device)
+        ex = G.export()
+        o = np.lexsort((g.dst, g.src))
+        np.testing.assert_array_equal(ex["out_adj"], g.dst[o])
+        np.testing.assert_array_equal(ex["out_elab"], g.elab[o])
+        np.testing.assert_array_equal(ex["out_off"], np.concatenate([[0], np.cumsum(np.bincount(g.src, minlength=g.n))]))
+        i = np.lexsort((g.src, g.dst))
+        np.testing.assert_array_equal(ex["in_adj"], g.src[i])
+        np.testing.assert_array_equal(ex["in_elab"], g.elab[i])
+        np.testing.assert_array_equal(ex["in_off"], np.concatenate([[0], np.cumsum(np.bincount(g.dst, minlength=g.n))]))
+
+
+def test_graph_build_rmat_hubs(hm):
+    g = synth.config2_graph(scale=14)
+    ex = hm.Graph.from_synth(g).export()
+    o = np.lexsort((g.dst, g.src))
+    np.testing.assert_array_equal(ex["out_adj"], g.dst[o])
+    np.testing.assert_array_equal(ex["out_elab"], g.elab[o])
+
+
+def _export_groups(hm, G):
+    import ctypes
+    n, m = G.n, G.m
+    nd = np.zeros(2, np.int64)
+    hm.check(hm.lib.hm_graph_export_groups(G.handle, None, None, None, None, None,
+                                           ctypes.c_void_p(nd.ctypes.data)), "groups")
+    out = {"gout": np.zeros(max(m, 1), np.int32), "gin": np.zeros(max(m, 1), np.int32),
+           "vdir": np.zeros((max(n, 1), 4), np.int32),
+           "dout": np.zeros((max(int(nd[0]), 1), 4), np.int32),
+           "din": np.zeros((max(int(nd[1]), 1), 4), np.int32)}
+    hm.check(hm.lib.hm_graph_export_groups(G.handle, *[ctypes.c_void_p(out[k].ctypes.data) for k in
+                                                       ("gout", "gin", "vdir", "dout", "din")],
+                                           None), "groups")
+    return out, nd
+
+
+@pytest.mark.parametrize("signed_labels", [False, True])
+def test_label_grouped_lists_and_directory(hm, signed_labels):
+    g = synth.config2_graph(scale=10)
+    if signed_labels:   # labels outside [0, 2^24) take the 32-bit key path
+        g = synth.Graph(g.n, g.src, g.dst, (g.vlab * 1000003 - 5).astype(np.int32),
+                        (g.elab * -7).astype(np.int32))
+    G = hm.Graph.from_synth(g)
+    ex = G.export()
+    gr, nd = _export_groups(hm, G)
+    for side, key, other, off in (("out", g.src, g.dst, ex["out_off"]), ("in", g.dst, g.src, ex["in_off"])):
+        o = np.lexsort((other, g.vlab[other], g.elab, key))
+        glist = gr["gout" if side == "out" else "gin"][: g.m]
+        np.testing.assert_array_equal(glist, other[o])
+        ks, el, vl = key[o], g.elab[o], g.vlab[other][o]
+        starts = np.flatnonzero(np.r_[True, (ks[1:] != ks[:-1]) | (el[1:] != el[:-1]) | (vl[1:] != vl[:-1])])
+        ends = np.r_[starts[1:], g.m]
+        d = gr["dout" if side == "out" else "din"][: starts.shape[0]]
+        assert int(nd[0 if side == "out" else 1]) == starts.shape[0]
+        np.testing.assert_array_equal(d[:, 0], el[starts])
+        np.testing.assert_array_equal(d[:, 1], vl[starts])
+        np.testing.assert_array_equal(d[:, 2], starts - off[ks[starts]])
+        np.testing.assert_array_equal(d[:, 3], ends - off[ks[starts]])
+        col = 0 if side == "out" else 2
+        first = np.searchsorted(starts, off[:-1])
+        cnt = np.searchsorted(starts, off[1:]) - first
+        np.testing.assert_array_equal(gr["vdir"][: g.n, col], first)
+        np.testing.assert_array_equal(gr["vdir"][: g.n, col + 1], cnt)
+
+
+def test_graph_build_edge_cases(hm):
+    G = hm.Graph(5, [], [], [0] * 5, [])            # no arcs
+    ex = G.export()
+    assert ex["out_off"].tolist() == [0] * 6 and ex["in_off"].tolist() == [0] * 6
+    G = hm.Graph(0, [], [], [], [])                  # empty graph
+    assert G.n == 0
+    G = hm.Graph(4, [3], [0], [1, 2, 3, 4], [9])      # isolated vertices around one arc
+    ex = G.export()
+    assert ex["out_off"].tolist() == [0, 0, 0, 0, 1]
+    assert ex["in_off"].tolist() == [0, 1, 1, 1, 1]
+    for src, dst, status in ([[0, 1], [1, 1], "HM_ERR_SELF_LOOP"],
+                             [[0, 0], [1, 1], "HM_ERR_DUP_EDGE"],
+                             [[0, 7], [1, 2], "HM_ERR_ARG"]):
+        with pytest.raises(hm.HMError) as ei:
+            hm.Graph(3, src, dst, [0, 0, 0], [0] * len(src))
+        assert ei.value.status == getattr(hm.binding, status)
+
+
+# ---------------------------------------------------------------------------
+# injected states (Alg. 2 + Alg. 3 inside the edge loop)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_injected_states_equal_plain_validators(hm, seed):
+    rng = np.random.default_rng(seed)
+    g = synth.er_graph(300, 6000, 2, 2, seed=100 + seed) if seed % 2 else \
+        synth.small_random_graph(40, 0.3, 2, 2, seed=seed, recip=0.5, hub=True)
+    G = hm.Graph.from_synth(g)
+    for t in range(6):
+        k = int(rng.integers(2, 6))
+        sp = synth.random_pattern(rng, k, float(rng.uniform(0.3, 0.9)), n_vlab=2, n_elab=2)
+        P = hm.Pattern.from_synth(sp)
+        for mode in MODES:
+            want = steps.injected_states(g, sp, bool(mode))
+            got = hm.injected_states(G, P, mode).cpu().numpy()
+            got = got[np.lexsort((got[:, 1], got[:, 0]))] if got.shape[0] else got.reshape(0, 2)
+            np.testing.assert_array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------
+# full matching, small and medium inputs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", _golden.match_cases(), ids=lambda c: c.name)
+def test_hand_worked(hm, case):
+    G = hm.Graph.from_synth(case.graph())
+    P = hm.Pattern.from_synth(case.pattern())
+    for mode_name, (count, rows) in case.expect.items():
+        mode = oracle.MONO if mode_name == "mono" else oracle.INDUCED
+        assert hm.count_matches(G, P, mode) == count
+        got = hm.enumerate_matches(G, P, mode).cpu().numpy()
+        np.testing.assert_array_equal(got, np.array(rows, np.int32).reshape(-1, case.k))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_graphs(hm, seed):
+    rng = np.random.default_rng(2000 + seed)
+    g = synth.small_random_graph(int(rng.integers(6, 40)), float(rng.uniform(0.1, 0.6)),
+                                 int(rng.integers(1, 3)), int(rng.integers(1, 3)), seed=seed,
+                                 recip=float(rng.uniform(0, 0.7)), hub=seed % 2 == 0)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    for t in range(8):
+        k = int(rng.integers(2, 7))
+        sp = synth.random_pattern(rng, k, float(rng.uniform(0.2, 1.0)), n_vlab=int(g.vlab.max()) + 1,
+                                  n_elab=int(g.elab.max()) + 1)
+        for mode in MODES:
+            _check(hm, G, og, sp, mode)
+
+
+def test_complete_digraph(hm):
+    g = synth.complete_digraph(9)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    rng = np.random.default_rng(0)
+    for k in (2, 3, 4, 5):
+        sp = synth.random_pattern(rng, k, 0.5, n_vlab=1, n_elab=1)
+        for mode in MODES:
+            _check(hm, G, og, sp, mode)
+
+
+def test_er_workload_cycle3(hm):
+    """1,000-vertex ER workload: labelled 3-cycle (count + rows) and its unlabelled count."""
+    g = synth.config1_graph()
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    sp = synth.config1_pattern()
+    for mode in MODES:
+        _check(hm, G, og, sp, mode)
+    gu = synth.Graph(g.n, g.src, g.dst, np.zeros(g.n, np.int32), np.zeros(g.m, np.int32))
+    Gu = hm.Graph.from_synth(gu)
+    ogu = oracle.OracleGraph.from_synth(gu)
+    spu = synth.Pattern(3, sp.src, sp.dst, np.zeros(3, np.int32), np.zeros(3, np.int32), "cycle3u")
+    c = _check(hm, Gu, ogu, spu, oracle.MONO)
+    assert c > 0
+
+
+@pytest.mark.parametrize("scale", [10, 13])
+def test_rmat_reduced_three_motifs(hm, scale):
+    g = synth.config2_graph(scale=scale)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    for sp in synth.config2_patterns():
+        for mode in MODES:
+            _check(hm, G, og, sp, mode)
+
+
+def test_rmat_reduced_random_batch_patterns(hm):
+    g = synth.config2_graph(scale=12)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    for sp in synth.config4_patterns(count=40):
+        _check(hm, G, og, sp, oracle.INDUCED)
+        _check(hm, G, og, sp, oracle.MONO, rows=False)
+
+
+def test_connectome_reduced(hm):
+    g = synth.config3_graph(n=3000, n_unique=120_000, n_recip=6000)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    for sp in synth.config3_patterns():
+        _check(hm, G, og, sp, oracle.MONO, rows=False)
+        _check(hm, G, og, sp, oracle.INDUCED)
+
+
+def test_unlabelled_hubs_force_donation(hm):
+    """Power-law graph, one label: a few seeds own most of the work, so warps must share it."""
+    g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
+    g = synth.Graph(g0.n, g0.src, g0.dst, np.zeros(g0.n, np.int32), np.zeros(g0.m, np.int32))
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    sp = synth.Pattern(4, np.array([0, 1, 2], np.int32), np.array([1, 2, 3], np.int32),
+                       np.zeros(4, np.int32), np.zeros(3, np.int32), "path4")
+    _check(hm, G, og, sp, oracle.MONO, rows=False)
+    st = hm.last_stats()
+    assert st["tasks_donated"] > 0
+
+
+# ---------------------------------------------------------------------------
+# API behaviour on the device
+# ---------------------------------------------------------------------------
+
+def test_capacity_protocol(hm):
+    g = synth.er_graph(200, 3000, 1, 1, seed=5)
+    G = hm.Graph.from_synth(g)
+    sp = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
+                       np.zeros(3, np.int32), np.zeros(2, np.int32))
+    P = hm.Pattern.from_synth(sp)
+    total = hm.count_matches(G, P, hm.MONO)
+    assert total > 10
+    buf = torch.empty(10 * 3, dtype=torch.int32, device="cuda")
+    with pytest.raises(hm.HMError) as ei:
+        hm.enumerate_matches(G, P, hm.MONO, out=buf, capacity=10)
+    assert ei.value.status == hm.binding.HM_ERR_CAPACITY and ei.value.count == total
+    rows = hm.enumerate_matches(G, P, hm.MONO, capacity=total)
+    assert rows.shape == (total, 3)
+
+
+def test_budget_watchdog_then_recovery(hm):
+    g = synth.er_graph(2000, 60000, 1, 1, seed=6)
+    G = hm.Graph.from_synth(g)
+    sp = synth.Pattern(4, np.array([0, 1, 2], np.int32), np.array([1, 2, 3], np.int32),
+                       np.zeros(4, np.int32), np.zeros(3, np.int32))
+    P = hm.Pattern.from_synth(sp)
+    full = hm.count_matches(G, P, hm.MONO)
+    hm.set_budget(60_000, 64)
+    try:
+        with pytest.raises(hm.HMError) as ei:
+            hm.count_matches(G, P, hm.MONO)
+        assert ei.value.status == hm.binding.HM_ERR_BUDGET
+    finally:
+        hm.set_budget(60_000, 0)
+    assert hm.count_matches(G, P, hm.MONO) == full
+
+
+def test_rooted_counts_partition(hm):
+    g = synth.config2_graph(scale=11)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    rng = np.random.default_rng(3)
+    for sp in synth.config2_patterns():
+        P = hm.Pattern.from_synth(sp)
+        total = hm.count_matches(G, P, hm.INDUCED)
+        part = rng.integers(0, 3, g.n)
+        for root in range(sp.k):
+            s = 0
+            for i in range(3):
+                mask = (part == i).astype(np.uint8)
+                c = hm.count_matches_rooted(G, P, hm.INDUCED, root, mask)
+                if root == 0:
+                    assert c == og.match(sp, oracle.INDUCED, rows=False, root_mask=mask)[0]
+                s += c
+            assert s == total
+
+
+def test_empty_and_label_free_results(hm):
+    g = synth.er_graph(100, 500, 2, 2, seed=8)
+    G = hm.Graph.from_synth(g)
+    sp = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
+                       np.array([7, 7, 7], np.int32), np.zeros(2, np.int32))   # label absent
+    P = hm.Pattern.from_synth(sp)
+    assert hm.count_matches(G, P, hm.MONO) == 0
+    assert hm.enumerate_matches(G, P, hm.MONO).shape == (0, 3)
+    E = hm.Graph(50, [], [], [0] * 50, [])
+    assert hm.count_matches(E, P, hm.MONO) == 0
+
+
+def test_stream_ordering_on_side_stream(hm):
+    g = synth.er_graph(500, 8000, 2, 2, seed=9)
+    og = oracle.OracleGraph.from_synth(g)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        G = hm.Graph.from_synth(g, stream=s)
+        sp = synth.config1_pattern()
+        P = hm.Pattern.from_synth(sp)
+        rows = hm.enumerate_matches(G, P, hm.MONO, stream=s)
+        host = rows.cpu().numpy()
+    np.testing.assert_array_equal(host, og.match(sp, oracle.MONO)[1])
