@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Benchmark: matches/s and per-query latency of the subgraph-matching hot path on GB300.
+
+One step = one pass of the whole hot path over the R-MAT workload: the three
+4-vertex induced motifs (feed-forward loop plus out-edge, bi-fan, 4-cycle;
+vertex labels (0,1,0,1), arc labels 0), each query running the edge scan with
+both validators, state injection, the persistent extension and the row sort,
+and returning its count and its sorted rows.  Target: R-MAT scale 20 (2^24
+samples, (a,b,c,d) = (.57,.19,.19,.05), duplicates and self-loops removed,
+~16.09M arcs), Zipf(1.2) vertex labels over 8 values, arc labels over 4.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) each rank handles one
+contiguous range of the target's arcs as seeds (hm_*_part) and the match
+counts are summed with one all-reduce per step; time is the max over ranks.
+The reference arm times the CPU oracle on a bounded sample of the same
+workload (queries restricted to a seeded subset of root vertices).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "matches/sec and query latency (p50/p99) on 1 GB300, batched vs single-query"
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the full workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args(argv)
+
+
+def workload_config(g, scale):
+    return {
+        "workload": (f"R-MAT scale {scale} ({g.n:,} vertices, {g.m:,} arcs after dedup), Zipf(1.2) "
+                     "vertex labels over 8, arc labels over 4; induced 4-vertex motifs ffl_out, bifan, "
+                     "cycle4 with vertex labels (0,1,0,1) and arc labels 0; count + sorted rows per query"),
+        "graph": "rmat", "scale": scale, "n": g.n, "m": g.m,
+        "patterns": ["ffl_out", "bifan", "cycle4"], "mode": "induced",
+        "queries_per_step": 3,
+        "l2": "flushed between steps (256 MiB device write outside the timed events); graph > L2",
+    }
+
+
+# ---------------------------------------------------------------------------
+# measured peaks and committed ncu figures
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2507_04130_gb300", "csrc", "hm_match.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload_key):
+    """DRAM bytes per launch from profiles/<kernel>_<workload>.md, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_key}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    src = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    per = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not src or not per or src.group(1) != kernel_source_hash():
+        return None
+    return float(per.group(1))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+        except Exception:
+            pass
+        if uuid:
+            cmd += ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(g, pats, mode, target_s, seed=0, og=None):
+    """Time the oracle on the workload restricted to a seeded random subset of root vertices.
+
+    Returns (matches, seconds, roots, threads).  The root set is grown until the
+    sample costs about `target_s` seconds of wall time.
+    """
+    import numpy as np
+
+    import oracle
+
+    og = og or oracle.OracleGraph.from_synth(g)
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(g.n)
+    roots = 1024
+    while True:
+        mask = np.zeros(g.n, np.uint8)
+        mask[perm[:roots]] = 1
+        t0 = time.perf_counter()
+        total = 0
+        for p in pats:
+            total += og.match(p, mode, rows=False, threads=threads, root_mask=mask)[0]
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or roots >= g.n:
+            return total, dt, roots, threads, og
+        grow = max(2.0, min(16.0, 0.8 * target_s / max(dt, 1e-3)))
+        roots = min(g.n, int(roots * grow))
+
+
+# ---------------------------------------------------------------------------
+# cross-rank reduction (time = max over ranks, matches = sum)
+# ---------------------------------------------------------------------------
+
+def reduce_over_ranks(total_ms: float, matches: int, dist=None, device=None):
+    """Whole-job figures: the slowest rank's time and the matches all ranks found."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_ms), int(matches)
+    import torch
+
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    m = torch.tensor([int(matches)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(m.item())
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import synth
+    import paper_2507_04130_gb300 as hm
+
+    g = synth.cached("rmat", synth.config2_graph, scale=args.scale)
+    spats = synth.config2_patterns()
+    mode = hm.INDUCED
+    G = hm.Graph.from_synth(g)
+    P = [hm.Pattern.from_synth(p) for p in spats]
+    stream = torch.cuda.current_stream()
+
+    counts = [hm.count_matches_part(G, p, mode, rank, world) for p in P]
+    bufs = [torch.empty(max(c, 1) * p.k, dtype=torch.int32, device="cuda") for c, p in zip(counts, P)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def query(i):
+        return hm.enumerate_matches_part(G, P[i], mode, rank, world, bufs[i])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    hm.set_timing(True)
+    for _ in range(args.warmup):
+        for i in range(len(P)):
+            query(i)
+    torch.cuda.synchronize()
+    barrier()
+
+    clocks = ClockSampler(local).start()
+    time.sleep(0.3)   # let the sampler start before the timed region
+    events, ext_ms, edge_ms, sort_ms = [], [[] for _ in P], [[] for _ in P], [[] for _ in P]
+    launches, matches = 0, 0
+    torch.cuda.synchronize()
+    barrier()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        for i in range(len(P)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rows = query(i)
+            e1.record(stream)
+            st = hm.last_stats()
+            launches += int(st["kernel_launches"])
+            ext_ms[i].append(st["ms_extend"])
+            edge_ms[i].append(st["ms_edge_scan"])
+            sort_ms[i].append(st["ms_sort"])
+            matches += int(rows.shape[0])
+            events.append((s, i, e0, e1))
+        if dist is not None:
+            t = torch.tensor([matches], dtype=torch.int64, device="cuda")
+            dist.all_reduce(t)   # the one exchange per step: total match count
+    torch.cuda.synchronize()
+    barrier()
+    clock = clocks.stop()
+    hm.set_timing(False)
+
+    q_ms = [e0.elapsed_time(e1) for _, _, e0, e1 in events]
+    total_ms = sum(q_ms)
+    step_ms = [sum(q_ms[j] for j, (s, _, _, _) in enumerate(events) if s == k) for k in range(args.steps)]
+    total_ms, all_matches = reduce_over_ranks(total_ms, matches, dist, "cuda")
+    value = all_matches / (total_ms / 1e3)
+
+    # algorithmic bytes of each kernel: one instrumented pass (not timed)
+    hm.set_counters(True)
+    bytes_ext, bytes_edge = [], []
+    for i in range(len(P)):
+        query(i)
+        st = hm.last_stats()
+        bytes_ext.append(int(st["bytes_extend"]))
+        bytes_edge.append(int(st["bytes_edge_scan"]))
+    hm.set_counters(False)
+
+    peak, peak_src = hbm_peak()
+    mean_ext = [statistics.mean(x) for x in ext_ms]
+    mean_edge = [statistics.mean(x) for x in edge_ms]
+    achieved_ext = sum(bytes_ext) / (sum(mean_ext) / 1e3) / 1e9
+    achieved_edge = sum(bytes_edge) / (sum(mean_edge) / 1e3) / 1e9
+    workload_key = f"rmat{args.scale}"
+    traffic = committed_traffic("k_extend", workload_key)
+    roofline = {
+        "bound": "hbm", "kernel": "k_extend", "achieved": round(achieved_ext, 2), "peak": peak,
+        "unit": "GB/s", "frac": round(achieved_ext / peak, 4),
+        "traffic": traffic, "peak_source": peak_src,
+        "algorithmic_bytes_per_launch": [int(b) for b in bytes_ext],
+        "mean_launch_ms": [round(x, 4) for x in mean_ext],
+        "kernels": {
+            "k_extend": {"ms_per_step": round(sum(mean_ext), 4), "GBps": round(achieved_ext, 2)},
+            "k_edge_seed": {"ms_per_step": round(sum(mean_edge), 4), "GBps": round(achieved_edge, 2),
+                            "frac": round(achieved_edge / peak, 4),
+                            "algorithmic_bytes_per_launch": bytes_edge},
+            "row_sort": {"ms_per_step": round(sum(statistics.mean(x) for x in sort_ms), 4)},
+        },
+    }
+
+    # end to end through the public API: host pattern arrays in, host rows out
+    pinned = [torch.empty(max(c, 1) * p.k, dtype=torch.int32, pin_memory=True) for c, p in zip(counts, P)]
+    bi = bo = 0
+    e2e_matches = 0
+    torch.cuda.synchronize()
+    e2e_s = 0.0
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, sp in enumerate(spats):
+            arrays = [np.asarray(a, np.int32) for a in (sp.src, sp.dst, sp.vlab, sp.elab)]
+            bi += sum(a.nbytes for a in arrays)
+            Pq = hm.Pattern(sp.k, *arrays)
+            rows = hm.enumerate_matches_part(G, Pq, mode, rank, world, bufs[i])
+            n = rows.numel()
+            pinned[i][:n].copy_(rows.view(-1), non_blocking=True)
+            bo += n * 4 + 8
+            e2e_matches += rows.shape[0]
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+    e2e_s, e2e_matches = reduce_over_ranks(e2e_s, e2e_matches, dist, "cuda")
+    e2e = {"value": round(e2e_matches / e2e_s, 1), "unit": "matches/s",
+           "h2d_bytes_per_step": bi // args.steps, "d2h_bytes_per_step": bo // args.steps,
+           "path": "hm.Pattern from host arrays + hm_enumerate_matches_part + D2H to pinned host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m_cpu, t_cpu, roots, threads, _ = oracle_sample(g, spats, 1, args.cpu_seconds)
+        cpu = {"value": round(m_cpu / t_cpu, 1), "unit": "matches/s", "cores": threads,
+               "kind": "oracle",
+               "sample": (f"the 3 induced queries restricted to {roots:,} seeded random roots "
+                          f"(image of pattern vertex 0) of {g.n:,}; {m_cpu:,} matches in {t_cpu:.2f} s")}
+
+    if rank == 0:
+        lat = sorted(q_ms)
+        p50 = statistics.median(lat)
+        p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+        per_query = {sp.name: {"matches": counts[i] if world == 1 else None,
+                               "mean_ms": round(statistics.mean(q_ms[j] for j, ev in enumerate(events)
+                                                                if ev[1] == i), 3)}
+                     for i, sp in enumerate(spats)}
+        cfg = workload_config(g, args.scale)
+        cfg["parallelism"] = f"{world} GPU(s), arc-range partition of the seeds" if world > 1 else "single GPU"
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "matches/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic", "config": cfg,
+            "latency_ms": {"p50": round(p50, 3), "p99": round(p99, 3), "queries": len(lat),
+                           "per_query": per_query},
+            "step_ms": [round(x, 3) for x in step_ms],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clock,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands, on a bounded sample per step
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+
+    g = synth.cached("rmat", synth.config2_graph, scale=args.scale)
+    spats = synth.config2_patterns()
+    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    m0, t0, roots, threads, og = oracle_sample(g, spats, 1, per_step)
+    import numpy as np
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(g.n)
+    total_m, total_s = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        mask = np.zeros(g.n, np.uint8)
+        mask[perm[(s * roots) % g.n:][:roots]] = 1
+        t = time.perf_counter()
+        c = sum(og.match(p, 1, rows=True, threads=threads, root_mask=mask)[0] for p in spats)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            total_m += c
+            total_s += dt
+    value = total_m / total_s if total_s > 0 else 0.0
+    sample = (f"each step: the 3 induced queries (count + sorted rows) restricted to {roots:,} seeded "
+              f"random roots of {g.n:,}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "matches/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_s / max(args.steps, 1) * 1e3, 3),
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": workload_config(g, args.scale),
+        "cpu_baseline": {"value": round(value, 1), "unit": "matches/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": "matches/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -175,6 +175,21 @@ hm_status hm_count_matches_rooted(const hm_graph *g, const hm_pattern *p, hm_mod
                                   int32_t root, const uint8_t *root_mask_dev,
                                   uint64_t *count, void *stream);
 
+/* hm_count_matches_part / hm_enumerate_matches_part -- the same computation
+ * restricted to the depth-2 states seeded by target arcs of part `part` of
+ * `nparts` contiguous ranges of the CSR arc order (the HiPerMotif algorithm's
+ * parallel loop over target arcs, Sec. III-C, split into independent pieces).
+ * Part i covers arcs [s(i), s(i+1)) with s(i) = floor(m*i/nparts) rounded
+ * down to a multiple of 4 and s(nparts) = m.  Every match has exactly one
+ * seeding arc, so the parts' counts add up to the full count and their row
+ * sets are disjoint with the full row set as their union; each part's rows are
+ * sorted.  0 <= part < nparts, else HM_ERR_ARG.  Otherwise as the full calls. */
+hm_status hm_count_matches_part(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                int32_t part, int32_t nparts, uint64_t *count, void *stream);
+hm_status hm_enumerate_matches_part(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                    int32_t part, int32_t nparts, int32_t *rows_dev, uint64_t cap,
+                                    uint64_t *count, void *stream);
+
 /* hm_injected_states -- the depth-2 states the edge scan produces: every
  * target arc accepted by the vertex validator (Alg. 2) and the edge
  * validator (Alg. 3) for the reordered arc between positions 0 and 1, as
@@ -211,10 +226,23 @@ typedef struct {
   float ms_sort;            /* row sort (enumerate only)                    */
   int32_t extend_grid;      /* blocks of the extension launch               */
   int32_t extend_block;     /* threads per block                            */
+  uint32_t kernel_launches; /* kernels the call launched                    */
+  uint32_t pad;
+  /* algorithmic bytes each kernel requested (loads and stores the method
+   * needs, counted per access); filled only while counters are enabled */
+  uint64_t bytes_edge_scan;
+  uint64_t bytes_overlap;
+  uint64_t bytes_extend;
+  uint64_t candidates;      /* candidate vertices examined by the extension */
 } hm_stats;
 
 hm_status hm_last_stats(hm_stats *out);
 hm_status hm_set_timing(int enabled);
+
+/* Enable (1) or disable (0) the algorithmic-byte counters: matching calls then
+ * run instrumented kernel variants that tally the bytes they request into
+ * hm_stats.  For measurement only -- the instrumented variants are slower. */
+hm_status hm_set_counters(int enabled);
 
 #ifdef __cplusplus
 }

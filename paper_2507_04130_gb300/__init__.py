@@ -26,7 +26,8 @@ from .binding import HM_MONO as MONO
 from .binding import HMError, check, lib
 
 __all__ = ["Graph", "Pattern", "count_matches", "enumerate_matches", "count_matches_rooted",
-           "injected_states", "set_budget", "set_timing", "last_stats", "MONO", "INDUCED",
+           "count_matches_part", "enumerate_matches_part",
+           "injected_states", "set_budget", "set_timing", "set_counters", "last_stats", "MONO", "INDUCED",
            "HMError", "binding"]
 
 
@@ -188,6 +189,26 @@ def enumerate_matches(g: Graph, p: Pattern, mode: int, out: torch.Tensor | None 
     return out[: int(c.value) * k].view(int(c.value), k)
 
 
+def count_matches_part(g: Graph, p: Pattern, mode: int, part: int, nparts: int, stream=None) -> int:
+    """Matches seeded by part `part` of `nparts` contiguous ranges of the target's arcs."""
+    c = ctypes.c_uint64()
+    check(lib.hm_count_matches_part(g.handle, p.handle, int(mode), int(part), int(nparts),
+                                    ctypes.byref(c), _stream_ptr(stream)), "hm_count_matches_part")
+    return int(c.value)
+
+
+def enumerate_matches_part(g: Graph, p: Pattern, mode: int, part: int, nparts: int,
+                           out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Rows of the matches seeded by one arc range, written to `out` (sorted); raises on capacity."""
+    k = p.k
+    c = ctypes.c_uint64()
+    check(lib.hm_enumerate_matches_part(g.handle, p.handle, int(mode), int(part), int(nparts),
+                                        ctypes.c_void_p(out.data_ptr()), int(out.numel() // k),
+                                        ctypes.byref(c), _stream_ptr(stream)),
+          "hm_enumerate_matches_part", int(c.value))
+    return out[: int(c.value) * k].view(int(c.value), k)
+
+
 def count_matches_rooted(g: Graph, p: Pattern, mode: int, root: int, mask, stream=None) -> int:
     """Count only matches whose image of original pattern vertex `root` is flagged in mask (uint8[n])."""
     if not (isinstance(mask, torch.Tensor) and mask.is_cuda):
@@ -216,6 +237,11 @@ def set_budget(max_ms: int = 0, max_chunks: int = 0):
 
 def set_timing(enabled: bool):
     check(lib.hm_set_timing(1 if enabled else 0), "hm_set_timing")
+
+
+def set_counters(enabled: bool):
+    """Run instrumented kernels that tally algorithmic bytes (measurement only; slower)."""
+    check(lib.hm_set_counters(1 if enabled else 0), "hm_set_counters")
 
 
 def last_stats() -> dict:

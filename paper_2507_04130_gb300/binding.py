@@ -21,8 +21,9 @@ EXPORTED = [
     "hm_status_str", "hm_load_graph", "hm_free_graph", "hm_graph_info", "hm_graph_export",
     "hm_graph_export_groups",
     "hm_load_pattern", "hm_free_pattern", "hm_pattern_order", "hm_count_matches",
-    "hm_enumerate_matches", "hm_count_matches_rooted", "hm_injected_states", "hm_set_budget",
-    "hm_last_stats", "hm_set_timing",
+    "hm_enumerate_matches", "hm_count_matches_rooted", "hm_count_matches_part",
+    "hm_enumerate_matches_part", "hm_injected_states", "hm_set_budget",
+    "hm_last_stats", "hm_set_timing", "hm_set_counters",
 ]
 
 
@@ -39,6 +40,12 @@ class hm_stats(ctypes.Structure):
         ("ms_sort", ctypes.c_float),
         ("extend_grid", ctypes.c_int32),
         ("extend_block", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("bytes_edge_scan", ctypes.c_uint64),
+        ("bytes_overlap", ctypes.c_uint64),
+        ("bytes_extend", ctypes.c_uint64),
+        ("candidates", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -68,9 +75,12 @@ _SIGS = {
     "hm_enumerate_matches": (_st, [_vp, _vp, ctypes.c_int, _vp, _u64, _pu64, _vp]),
     "hm_count_matches_rooted": (_st, [_vp, _vp, ctypes.c_int, _i32, _vp, _pu64, _vp]),
     "hm_injected_states": (_st, [_vp, _vp, ctypes.c_int, _vp, _u64, _pu64, _vp]),
+    "hm_count_matches_part": (_st, [_vp, _vp, ctypes.c_int, _i32, _i32, _pu64, _vp]),
+    "hm_enumerate_matches_part": (_st, [_vp, _vp, ctypes.c_int, _i32, _i32, _vp, _u64, _pu64, _vp]),
     "hm_set_budget": (_st, [_u64, _u64]),
     "hm_last_stats": (_st, [ctypes.POINTER(hm_stats)]),
     "hm_set_timing": (_st, [ctypes.c_int]),
+    "hm_set_counters": (_st, [ctypes.c_int]),
 }
 
 

@@ -8,6 +8,7 @@ namespace {
 std::atomic<uint64_t> g_budget_ms{120000};
 std::atomic<uint64_t> g_budget_chunks{0};
 std::atomic<int> g_timing{0};
+std::atomic<int> g_counters{0};
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -15,6 +16,7 @@ hm_stats &tls_stats() {
   return s;
 }
 bool timing_enabled() { return g_timing.load(std::memory_order_relaxed) != 0; }
+bool counters_enabled() { return g_counters.load(std::memory_order_relaxed) != 0; }
 uint64_t budget_ms() { return g_budget_ms.load(std::memory_order_relaxed); }
 uint64_t budget_chunks() { return g_budget_chunks.load(std::memory_order_relaxed); }
 }  // namespace hm
@@ -49,5 +51,10 @@ extern "C" hm_status hm_last_stats(hm_stats *out) {
 
 extern "C" hm_status hm_set_timing(int enabled) {
   hm::g_timing.store(enabled ? 1 : 0);
+  return HM_OK;
+}
+
+extern "C" hm_status hm_set_counters(int enabled) {
+  hm::g_counters.store(enabled ? 1 : 0);
   return HM_OK;
 }

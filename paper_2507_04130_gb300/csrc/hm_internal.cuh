@@ -114,6 +114,28 @@ __device__ __forceinline__ int64_t search(const int32_t *__restrict__ a, int64_t
   return (i < end && __ldg(a + i) == x) ? i : -1;
 }
 
+// search() that also adds the bytes it reads to `bytes` when kCount is set
+// (the algorithmic-byte counters of an instrumented launch).
+template <bool kCount>
+__device__ __forceinline__ int64_t search_c(const int32_t *__restrict__ a, int64_t lo, int64_t len,
+                                            int32_t x, uint64_t &bytes) {
+  const int64_t end = lo + len;
+  while (len > 0) {
+    int64_t half = len >> 1;
+    int32_t v = __ldg(a + lo + half);
+    if (kCount) bytes += 4;
+    if (v < x) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  if (lo >= end) return -1;
+  if (kCount) bytes += 4;
+  return __ldg(a + lo) == x ? lo : -1;
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -161,6 +183,7 @@ namespace hm {
 // Thread-local record of the last call (hm_last_stats).
 hm_stats &tls_stats();
 bool timing_enabled();
+bool counters_enabled();
 uint64_t budget_ms();
 uint64_t budget_chunks();
 

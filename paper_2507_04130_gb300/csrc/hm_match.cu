@@ -66,6 +66,10 @@ struct Ctl {
   unsigned long long rows_written;
   unsigned long long chunks;
   unsigned long long donated;
+  unsigned long long bytes_edge;     // algorithmic bytes (instrumented launches only)
+  unsigned long long bytes_overlap;
+  unsigned long long bytes_extend;
+  unsigned long long lanes;          // candidates examined (instrumented launches only)
   int32_t active;
   int32_t hungry;
   int32_t status;
@@ -95,19 +99,23 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t *p) {
 // ---------------------------------------------------------------------------
 // arc lookup: is (x -> y) an arc?  Searches the shorter of out(x) and in(y).
 // ---------------------------------------------------------------------------
+template <bool kC>
 __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t y, int32_t outdeg_x,
-                                           int32_t indeg_y, int32_t *lab) {
+                                           int32_t indeg_y, int32_t *lab, uint64_t &ctr) {
   if (outdeg_x == 0 || indeg_y == 0) return false;
+  if (kC) ctr += 8;
   if (outdeg_x <= indeg_y) {
     int64_t o = __ldg(&G.off[x].x);
-    int64_t i = search(G.out_adj, o, outdeg_x, y);
+    int64_t i = search_c<kC>(G.out_adj, o, outdeg_x, y, ctr);
     if (i < 0) return false;
+    if (kC) ctr += 4;
     *lab = __ldg(G.out_elab + i);
     return true;
   }
   int64_t o = __ldg(&G.off[y].y);
-  int64_t i = search(G.in_adj, o, indeg_y, x);
+  int64_t i = search_c<kC>(G.in_adj, o, indeg_y, x, ctr);
   if (i < 0) return false;
+  if (kC) ctr += 4;
   *lab = __ldg(G.in_elab + i);
   return true;
 }
@@ -115,13 +123,17 @@ __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t
 // ---------------------------------------------------------------------------
 // edge scan: vertex validator + edge validator (label, opposite arc, degrees)
 // ---------------------------------------------------------------------------
+template <bool kC>
 __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int32_t a, int32_t b,
-                                          int32_t l, const uint8_t *root_mask, int2 *out) {
+                                          int32_t l, const uint8_t *root_mask, int2 *out,
+                                          uint64_t &ctr) {
   if (l != P.seed_lab) return false;                       // match(e1, e2)
   const int32_t u = P.seed_rev ? b : a;                     // image of position 0
   const int32_t v = P.seed_rev ? a : b;                     // image of position 1
+  if (kC) ctr += 16;
   const int4 iu = __ldg(&G.vi[u]);                          // Alg. 2 on u
   if (iu.x != P.vlab[0] || iu.y < P.dout[0] || iu.z < P.din[0]) return false;
+  if (kC) ctr += 16;
   const int4 iv = __ldg(&G.vi[v]);                          // match(v, 1) + degrees
   if (iv.x != P.vlab[1] || iv.y < P.dout[1] || iv.z < P.din[1]) return false;
   if (root_mask && ((P.root_pos == 0 && !root_mask[u]) || (P.root_pos == 1 && !root_mask[v])))
@@ -131,26 +143,31 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
     const int4 ib = P.seed_rev ? iu : iv;
     const int4 ia = P.seed_rev ? iv : iu;
     int32_t lab = 0;
-    bool found = arc_lookup(G, b, a, ib.y, ia.z, &lab);
+    bool found = arc_lookup<kC>(G, b, a, ib.y, ia.z, &lab, ctr);
     if (P.back_req && (!found || lab != P.back_lab)) return false;
     if (P.back_forbid && found) return false;
   }
   *out = make_int2(u, v);
+  if (kC) ctr += 8;
   return true;
 }
 
+template <bool kC>
 __global__ void __launch_bounds__(kSeedThreads)
 k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
             const uint8_t *__restrict__ root_mask, int2 *__restrict__ seeds,
-            unsigned long long cap, unsigned long long *__restrict__ nseeds) {
+            unsigned long long cap, unsigned long long *__restrict__ nseeds,
+            unsigned long long *__restrict__ bytes, int64_t e_begin, int64_t e_end) {
+  uint64_t ctr = 0;
   __shared__ uint32_t s_warp[kSeedThreads / 32];
   __shared__ unsigned long long s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ngroups = (G.m + 3) >> 2;
-  const int64_t full_groups = G.m >> 2;
-  const int4 *src4 = reinterpret_cast<const int4 *>(G.src);
-  const int4 *dst4 = reinterpret_cast<const int4 *>(G.out_adj);
-  const int4 *lab4 = reinterpret_cast<const int4 *>(G.out_elab);
+  // arcs [e_begin, e_end), e_begin a multiple of 4 so the int4 streams stay aligned
+  const int64_t ngroups = (e_end - e_begin + 3) >> 2;
+  const int64_t full_groups = (e_end - e_begin) >> 2;
+  const int4 *src4 = reinterpret_cast<const int4 *>(G.src + e_begin);
+  const int4 *dst4 = reinterpret_cast<const int4 *>(G.out_adj + e_begin);
+  const int4 *lab4 = reinterpret_cast<const int4 *>(G.out_elab + e_begin);
   for (int64_t g0 = (int64_t)blockIdx.x * kSeedThreads; g0 < ngroups;
        g0 += (int64_t)gridDim.x * kSeedThreads) {
     const int64_t gi = g0 + threadIdx.x;
@@ -158,14 +175,17 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     bool ok[4] = {false, false, false, false};
     if (gi < full_groups) {
       int4 a = __ldcs(src4 + gi), b = __ldcs(dst4 + gi), l = __ldcs(lab4 + gi);
-      ok[0] = seed_test(G, P, a.x, b.x, l.x, root_mask, &s[0]);
-      ok[1] = seed_test(G, P, a.y, b.y, l.y, root_mask, &s[1]);
-      ok[2] = seed_test(G, P, a.z, b.z, l.z, root_mask, &s[2]);
-      ok[3] = seed_test(G, P, a.w, b.w, l.w, root_mask, &s[3]);
+      if (kC) ctr += 48;
+      ok[0] = seed_test<kC>(G, P, a.x, b.x, l.x, root_mask, &s[0], ctr);
+      ok[1] = seed_test<kC>(G, P, a.y, b.y, l.y, root_mask, &s[1], ctr);
+      ok[2] = seed_test<kC>(G, P, a.z, b.z, l.z, root_mask, &s[2], ctr);
+      ok[3] = seed_test<kC>(G, P, a.w, b.w, l.w, root_mask, &s[3], ctr);
     } else if (gi < ngroups) {
       for (int j = 0; j < 4; ++j) {
-        int64_t e = gi * 4 + j;
-        if (e < G.m) ok[j] = seed_test(G, P, G.src[e], G.out_adj[e], G.out_elab[e], root_mask, &s[j]);
+        int64_t e = e_begin + gi * 4 + j;
+        if (kC && e < e_end) ctr += 12;
+        if (e < e_end)
+          ok[j] = seed_test<kC>(G, P, G.src[e], G.out_adj[e], G.out_elab[e], root_mask, &s[j], ctr);
       }
     }
     uint32_t cnt = (uint32_t)ok[0] + ok[1] + ok[2] + ok[3];
@@ -197,6 +217,10 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     }
     __syncthreads();
   }
+  if (kC) {
+    for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
+    if (lane == 0 && ctr) atomicAdd(bytes, (unsigned long long)ctr);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -204,22 +228,27 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
 // ---------------------------------------------------------------------------
 
 // Is w a neighbour (in or out) of y?
+template <bool kC>
 __device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, longlong2 oy,
-                                        int32_t w) {
-  if (iy.y && search(G.out_adj, oy.x, iy.y, w) >= 0) return true;
-  return iy.z && search(G.in_adj, oy.y, iy.z, w) >= 0;
+                                        int32_t w, uint64_t &ctr) {
+  if (iy.y && search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0) return true;
+  return iy.z && search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0;
 }
 
+template <bool kC>
 __global__ void __launch_bounds__(kSeedThreads)
 k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need, const int2 *__restrict__ in,
                const unsigned long long *__restrict__ nin, int2 *__restrict__ out,
-               unsigned long long cap, unsigned long long *__restrict__ nout) {
+               unsigned long long cap, unsigned long long *__restrict__ nout,
+               unsigned long long *__restrict__ bytes) {
+  uint64_t ctr = 0;
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n_in = (int64_t)*nin;
   for (int64_t s = wid; s < n_in; s += nw) {
     const int2 uv = in[s];
+    if (kC && lane == 0) ctr += 72;
     int4 iu = __ldg(&G.vi[uv.x]), iv = __ldg(&G.vi[uv.y]);
     longlong2 ou = __ldg(&G.off[uv.x]), ov = __ldg(&G.off[uv.y]);
     // iterate the side with fewer incident arcs, probe the other
@@ -233,7 +262,8 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need, const int2 *__r
       bool hit = false;
       if (b + lane < ix.y) {
         int32_t w = __ldg(G.out_adj + ox.x + b + lane);
-        hit = in_nbhd(G, y, iy, oy, w);
+        if (kC) ctr += 4;
+        hit = in_nbhd<kC>(G, y, iy, oy, w, ctr);
       }
       got += __popc(__ballot_sync(kFull, hit));
     }
@@ -242,15 +272,21 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need, const int2 *__r
       bool hit = false;
       if (b + lane < ix.z) {
         int32_t w = __ldg(G.in_adj + ox.y + b + lane);
-        bool dup = ix.y && search(G.out_adj, ox.x, ix.y, w) >= 0;
-        hit = !dup && in_nbhd(G, y, iy, oy, w);
+        if (kC) ctr += 4;
+        bool dup = ix.y && search_c<kC>(G.out_adj, ox.x, ix.y, w, ctr) >= 0;
+        hit = !dup && in_nbhd<kC>(G, y, iy, oy, w, ctr);
       }
       got += __popc(__ballot_sync(kFull, hit));
     }
     if (got >= need && lane == 0) {
       unsigned long long at = atomicAdd(nout, 1ull);
       if (at < cap) out[at] = uv;
+      if (kC) ctr += 8;
     }
+  }
+  if (kC) {
+    for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
+    if (lane == 0 && ctr) atomicAdd(bytes, (unsigned long long)ctr);
   }
 }
 
@@ -276,8 +312,10 @@ struct WarpState {
 // condition of the pattern, {first, length} of the matching label group inside
 // the anchor's list (first relative to the list start); Plan::gbase[p] indexes it.
 
+template <bool kC>
 __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int pos, int32_t c,
-                                           int lane) {
+                                           int lane, uint64_t &ctr) {
+  if (kC && lane == 0) ctr += 48;
   // three independent 16-byte loads spread over three lanes
   int4 vi = make_int4(0, 0, 0, 0), vd = make_int4(0, 0, 0, 0);
   longlong2 o = make_longlong2(0, 0);
@@ -302,12 +340,14 @@ __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int 
 }
 
 // Find the group (arc label, vertex label) in a directory span; {first, length} or {0, 0}.
+template <bool kC>
 __device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t first, int32_t cnt,
-                                           int32_t alab, int32_t vlab, int lane) {
+                                           int32_t alab, int32_t vlab, int lane, uint64_t &ctr) {
   for (int32_t b = 0; b < cnt; b += 32) {
     int4 e = make_int4(0, 0, 0, 0);
     bool hit = false;
     if (b + lane < cnt) {
+      if (kC) ctr += 16;
       e = __ldg(dir + first + b + lane);
       hit = e.x == alab && e.y == vlab;
     }
@@ -323,15 +363,17 @@ __device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t
 
 // Look up the label group of every anchor of position p; unless `keep`, pick the
 // smallest group as the driving range.
+template <bool kC>
 __device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, WarpState &S,
-                                            int2 *__restrict__ grp, int p, int lane, bool keep) {
+                                            int2 *__restrict__ grp, int p, int lane, bool keep,
+                                            uint64_t &ctr) {
   int best = 0;
   int32_t best_len = INT32_MAX;
   for (int j = 0; j < P.npos[p]; ++j) {
     const Cons cs = P.cons[p][j];
     const int4 d = S.dir[cs.q];
-    const int2 r = cs.kind == kOut ? dir_lookup(G.gdir_out, d.x, d.y, cs.lab, P.vlab[p], lane)
-                                   : dir_lookup(G.gdir_in, d.z, d.w, cs.lab, P.vlab[p], lane);
+    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G.gdir_out, d.x, d.y, cs.lab, P.vlab[p], lane, ctr)
+                                   : dir_lookup<kC>(G.gdir_in, d.z, d.w, cs.lab, P.vlab[p], lane, ctr);
     if (lane == 0) grp[P.gbase[p] + j] = r;
     if (r.y < best_len) {
       best_len = r.y;
@@ -351,10 +393,11 @@ __device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, Wa
 
 // Does candidate c (taken from the driving group, so its arc label and vertex
 // label already match) satisfy every other condition of position p?
+template <bool kC>
 __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P,
                                                 const WarpState &S, const int2 *__restrict__ grp,
                                                 int p, int drive, int32_t c, bool leaf,
-                                                const uint8_t *root_mask) {
+                                                const uint8_t *root_mask, uint64_t &ctr) {
   for (int i = 0; i < p; ++i)
     if (S.map[i] == c) return false;                        // injective
   if (root_mask && p == P.root_pos && !root_mask[c]) return false;
@@ -365,8 +408,10 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
   int4 vi = make_int4(0, 0, 0, 0);
   longlong2 oc = make_longlong2(0, 0);
   if (need_c) {
+    if (kC) ctr += 16;
     vi = __ldg(&G.vi[c]);
     if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
+    if (kC && nc > 1) ctr += 16;
     if (nc > 1) oc = __ldg(&G.off[c]);
   }
   for (int j = 0; j < nc; ++j) {
@@ -382,11 +427,13 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int32_t rev_len = fwd ? vi.z : vi.y;
       if (r.y == 0) return false;
       if (rev_len < r.y) {
-        const int64_t i = fwd ? search(G.in_adj, oc.y, rev_len, fq) : search(G.out_adj, oc.x, rev_len, fq);
+        const int64_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
+                              : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
+        if (kC && i >= 0) ctr += 4;
         found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
       } else {
         const int64_t base = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
-        found = search(fwd ? G.gout_adj : G.gin_adj, base, r.y, c) >= 0;
+        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, base, r.y, c, ctr) >= 0;
       }
       if (!found) return false;
     } else {
@@ -395,9 +442,9 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int32_t lb = fwd ? vi.z : vi.y;
       if (la == 0 || lb == 0) continue;
       if (la <= lb) {
-        found = search(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c) >= 0;
+        found = search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) >= 0;
       } else {
-        found = search(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq) >= 0;
+        found = search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) >= 0;
       }
       if (found) return false;
     }
@@ -535,10 +582,11 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int ngrp) {
   return (sizeof(WarpState) + sizeof(int2) * (size_t)ngrp + 15) / 16 * 16;
 }
 
-template <bool kRows>
+template <bool kRows, bool kC>
 __global__ void __launch_bounds__(kExtThreads)
 k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
          const __grid_constant__ ExtArgs A) {
+  uint64_t ctr = 0, lanes = 0;
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int lane = threadIdx.x & 31;
   const size_t stride = warp_smem_bytes(P.ngrp);
@@ -560,10 +608,11 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
       s = __shfl_sync(kFull, s, 0);
       if (s < nseeds) {
         const int2 uv = A.seeds[s];
-        set_mapped(G, S, 0, uv.x, lane);
-        set_mapped(G, S, 1, uv.y, lane);
+        if (kC && lane == 0) ctr += 8;
+        set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
+        set_mapped<kC>(G, S, 1, uv.y, lane, ctr);
         __syncwarp();
-        setup_level(G, P, S, grp, 2, lane, false);
+        setup_level<kC>(G, P, S, grp, 2, lane, false, ctr);
         got = 1;
       } else {
         seeds_done = true;
@@ -619,9 +668,9 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     if (got == 2) {
       // install a donated task
       const int d = S.stage.depth;
-      for (int i = 0; i < d; ++i) set_mapped(G, S, i, S.stage.map[i], lane);
+      for (int i = 0; i < d; ++i) set_mapped<kC>(G, S, i, S.stage.map[i], lane, ctr);
       __syncwarp();
-      setup_level(G, P, S, grp, d, lane, true);
+      setup_level<kC>(G, P, S, grp, d, lane, true, ctr);
       if (lane == 0) {
         S.drive[d] = S.stage.drive;
         S.lo[d] = S.stage.lo;
@@ -690,7 +739,11 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
         int32_t c = -1;
         if (idx < hi && ((allow >> lane) & 1u)) {
           c = __ldg(adj + idx);
-          ok = check_candidate(G, P, S, grp, level, drive, c, level == k - 1, A.root_mask);
+          if (kC) {
+            ctr += 4;
+            ++lanes;
+          }
+          ok = check_candidate<kC>(G, P, S, grp, level, drive, c, level == k - 1, A.root_mask, ctr);
         }
         const uint32_t m = __ballot_sync(kFull, ok);
         if (lane == 0) S.lo[level] = lo + 32;
@@ -705,6 +758,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
             if (ok) {
               unsigned long long r = at + __popc(m & lanemask_lt());
               if (r < A.cap) {
+                if (kC) ctr += 4 * k;
                 int32_t *row = A.rows + r * k;
                 for (int i = 0; i < k - 1; ++i) row[P.orig[i]] = S.map[i];
                 row[P.orig[k - 1]] = c;
@@ -729,10 +783,11 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
       const int32_t c = __ldg(adj + S.base[level] + b);
       __syncwarp();
       if (lane == 0) S.mask[level] = m & (m - 1);
-      set_mapped(G, S, level, c, lane);
+      if (kC && lane == 0) ctr += 4;
+      set_mapped<kC>(G, S, level, c, lane, ctr);
       __syncwarp();
       ++level;
-      setup_level(G, P, S, grp, level, lane, false);
+      setup_level<kC>(G, P, S, grp, level, lane, false, ctr);
       __syncwarp();
     }
   }
@@ -740,6 +795,16 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     if (!stop) atomicSub(&A.ctl->active, 1);
     if (my_count) atomicAdd(&A.ctl->count, my_count);
     if (my_chunks & 63) atomicAdd(&A.ctl->chunks, my_chunks & 63);
+  }
+  if (kC) {
+    for (int o = 16; o; o >>= 1) {
+      ctr += __shfl_xor_sync(kFull, ctr, o);
+      lanes += __shfl_xor_sync(kFull, lanes, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.ctl->bytes_extend, (unsigned long long)ctr);
+      atomicAdd(&A.ctl->lanes, (unsigned long long)lanes);
+    }
   }
 }
 
@@ -812,15 +877,22 @@ struct Scratch {
   }
 };
 
-// Resident blocks of the extension kernel for a given dynamic shared-memory size.
-int extend_grid(bool rows, size_t smem) {
-  static int cache[2][64] = {};
+using ExtendKernel = void (*)(DevGraph, Plan, ExtArgs);
+
+ExtendKernel extend_kernel(bool rows, bool counters) {
+  if (rows) return counters ? k_extend<true, true> : k_extend<true, false>;
+  return counters ? k_extend<false, true> : k_extend<false, false>;
+}
+
+// Resident blocks of an extension kernel variant for a dynamic shared-memory size.
+int extend_grid(bool rows, bool counters, size_t smem) {
+  static int cache[4][64] = {};
   const int slot = (int)std::min<size_t>(smem / 1024, 63);
-  int &c = cache[rows ? 1 : 0][slot];
+  int &c = cache[(rows ? 2 : 0) + (counters ? 1 : 0)][slot];
   if (!c) {
     int per_sm = 0;
-    cudaError_t e = rows ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend<true>, kExtThreads, smem)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend<false>, kExtThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, extend_kernel(rows, counters), kExtThreads, smem);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       return 0;
@@ -832,15 +904,24 @@ int extend_grid(bool rows, size_t smem) {
 
 enum class Want { kCount, kRows, kStates };
 
+// First arc of part `part` of `nparts` contiguous CSR ranges (multiple of 4; part == nparts gives m).
+int64_t part_start(int64_t m, int32_t part, int32_t nparts) {
+  if (part >= nparts) return m;
+  return (int64_t)((__int128)m * part / nparts) & ~int64_t(3);
+}
+
 hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_t root,
                     const uint8_t *root_mask, int32_t *out, uint64_t cap, uint64_t *count,
-                    cudaStream_t s, Want want) {
+                    cudaStream_t s, Want want, int32_t part = 0, int32_t nparts = 1) {
   if (!g || !p || !count || (mode != HM_MONO && mode != HM_INDUCED)) return HM_ERR_ARG;
+  if (nparts < 1 || part < 0 || part >= nparts) return HM_ERR_ARG;
   if (want != Want::kCount && cap > 0 && !out) return HM_ERR_ARG;
   ensure_pool();
   hm_stats &st = tls_stats();
   std::memset(&st, 0, sizeof(st));
   const bool timing = timing_enabled();
+  const bool counters = counters_enabled();
+  uint32_t launches = 0;
   Plan plan = p->plan[mode];
   if (root_mask) {
     if (root < 0 || root >= p->k) return HM_ERR_ARG;
@@ -861,12 +942,20 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
 
   // a2 + a3: edge scan with the vertex and edge validators
   Timer t_edge(s, timing);
+  const int64_t e_begin = part_start(m, part, nparts), e_end = part_start(m, part + 1, nparts);
   {
-    int64_t groups = (m + 3) / 4;
+    int64_t groups = (e_end - e_begin + 3) / 4;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + kSeedThreads - 1) / kSeedThreads,
                                                            (int64_t)sms * 8));
-    if (m) k_edge_seed<<<grid, kSeedThreads, 0, s>>>(G, plan, root_mask, seeds_a, (unsigned long long)m,
-                                                     &ctl->nseeds_raw);
+    if (e_end > e_begin) {
+      if (counters)
+        k_edge_seed<true><<<grid, kSeedThreads, 0, s>>>(G, plan, root_mask, seeds_a, (unsigned long long)m,
+                                                        &ctl->nseeds_raw, &ctl->bytes_edge, e_begin, e_end);
+      else
+        k_edge_seed<false><<<grid, kSeedThreads, 0, s>>>(G, plan, root_mask, seeds_a, (unsigned long long)m,
+                                                         &ctl->nseeds_raw, &ctl->bytes_edge, e_begin, e_end);
+      ++launches;
+    }
     t_edge.stop();
     HM_CUDA_TRY(cudaGetLastError());
   }
@@ -874,8 +963,15 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   const unsigned long long *nseeds = &ctl->nseeds_raw;
   Timer t_ov(s, timing && plan.ov_need > 0);
   if (plan.ov_need > 0) {
-    k_seed_overlap<<<sms * 8, kSeedThreads, 0, s>>>(G, plan.ov_need, seeds_a, &ctl->nseeds_raw, seeds_b,
-                                                    (unsigned long long)m, &ctl->nseeds);
+    if (counters)
+      k_seed_overlap<true><<<sms * 8, kSeedThreads, 0, s>>>(G, plan.ov_need, seeds_a, &ctl->nseeds_raw,
+                                                            seeds_b, (unsigned long long)m, &ctl->nseeds,
+                                                            &ctl->bytes_overlap);
+    else
+      k_seed_overlap<false><<<sms * 8, kSeedThreads, 0, s>>>(G, plan.ov_need, seeds_a, &ctl->nseeds_raw,
+                                                             seeds_b, (unsigned long long)m, &ctl->nseeds,
+                                                             &ctl->bytes_overlap);
+    ++launches;
     t_ov.stop();
     HM_CUDA_TRY(cudaGetLastError());
     seeds = seeds_b;
@@ -899,6 +995,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   Timer t_ext(s, timing && p->k > 2);
   if (p->k == 2) {
     k_seed_rows<<<sms * 4, 256, 0, s>>>(plan, seeds, nseeds, rows ? out : nullptr, cap, ctl);
+    ++launches;
     HM_CUDA_TRY(cudaGetLastError());
   } else {
     Task *qbuf;
@@ -906,6 +1003,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     HM_CUDA_TRY(sc.get((void **)&qbuf, sizeof(Task) * kQueueCap));
     HM_CUDA_TRY(sc.get((void **)&qseq, sizeof(unsigned long long) * kQueueCap));
     k_qinit<<<64, 256, 0, s>>>(qseq);
+    ++launches;
     ExtArgs A{};
     A.seeds = seeds;
     A.nseeds = nseeds;
@@ -918,12 +1016,12 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.budget_ns = budget_ms() * 1000000ull;
     A.max_chunks = budget_chunks();
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
-    const int grid = extend_grid(rows, smem);
+    const int grid = extend_grid(rows, counters, smem);
     if (grid <= 0) return HM_ERR_CUDA;
     st.extend_grid = grid;
     st.extend_block = kExtThreads;
-    if (rows) k_extend<true><<<grid, kExtThreads, smem, s>>>(G, plan, A);
-    else k_extend<false><<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    extend_kernel(rows, counters)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    ++launches;
     t_ext.stop();
     HM_CUDA_TRY(cudaGetLastError());
   }
@@ -933,11 +1031,16 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   st.ms_edge_scan = t_edge.ms();
   st.ms_overlap = t_ov.ms();
   st.ms_extend = t_ext.ms();
-  st.seeds_scanned = (uint64_t)m;
+  st.seeds_scanned = (uint64_t)(e_end - e_begin);
   st.states_injected = plan.ov_need > 0 ? h.nseeds : h.nseeds_raw;
   st.tasks_donated = h.donated;
   st.chunks = h.chunks;
   st.matches = h.count;
+  st.bytes_edge_scan = h.bytes_edge;
+  st.bytes_overlap = h.bytes_overlap;
+  st.bytes_extend = h.bytes_extend;
+  st.candidates = h.lanes;
+  st.kernel_launches = launches;
   if (h.status == kStatBudget) return HM_ERR_BUDGET;
   if (h.status != kStatOk) return HM_ERR_CUDA;
   *count = h.count;
@@ -949,7 +1052,9 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     HM_CUDA_TRY(sc.get((void **)&tmp, sizeof(int32_t) * (size_t)h.count * p->k));
     int cols[kMaxK];
     for (int i = 0; i < p->k; ++i) cols[i] = i;
-    hm_status r = radix_sort_rows(out, tmp, (int64_t)h.count, p->k, cols, p->k, bits_for(g->n), s);
+    const int sort_cols = p->k;
+    hm_status r = radix_sort_rows(out, tmp, (int64_t)h.count, p->k, cols, sort_cols, bits_for(g->n), s);
+    st.kernel_launches += 3 * ((sort_cols * bits_for(g->n) + 7) / 8);
     t.stop();
     if (r != HM_OK) return r;
     if (timing) {
@@ -982,6 +1087,20 @@ extern "C" hm_status hm_count_matches_rooted(const hm_graph *g, const hm_pattern
   if (!root_mask_dev) return HM_ERR_ARG;
   return run_match(g, p, mode, root, root_mask_dev, nullptr, 0, count, (cudaStream_t)stream,
                    Want::kCount);
+}
+
+extern "C" hm_status hm_count_matches_part(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                           int32_t part, int32_t nparts, uint64_t *count,
+                                           void *stream) {
+  return run_match(g, p, mode, -1, nullptr, nullptr, 0, count, (cudaStream_t)stream, Want::kCount,
+                   part, nparts);
+}
+
+extern "C" hm_status hm_enumerate_matches_part(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                               int32_t part, int32_t nparts, int32_t *rows_dev,
+                                               uint64_t cap, uint64_t *count, void *stream) {
+  return run_match(g, p, mode, -1, nullptr, rows_dev, cap, count, (cudaStream_t)stream, Want::kRows,
+                   part, nparts);
 }
 
 extern "C" hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mode,

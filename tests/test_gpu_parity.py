@@ -334,3 +334,47 @@ def test_stream_ordering_on_side_stream(hm):
         rows = hm.enumerate_matches(G, P, hm.MONO, stream=s)
         host = rows.cpu().numpy()
     np.testing.assert_array_equal(host, og.match(sp, oracle.MONO)[1])
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 8])
+def test_arc_range_parts_partition_the_matches(hm, nparts):
+    g = synth.config2_graph(scale=12)
+    G = hm.Graph.from_synth(g)
+    for sp in synth.config2_patterns():
+        P = hm.Pattern.from_synth(sp)
+        full = hm.enumerate_matches(G, P, hm.INDUCED).cpu().numpy()
+        parts, total = [], 0
+        for i in range(nparts):
+            c = hm.count_matches_part(G, P, hm.INDUCED, i, nparts)
+            buf = torch.empty(max(c, 1) * sp.k, dtype=torch.int32, device="cuda")
+            r = hm.enumerate_matches_part(G, P, hm.INDUCED, i, nparts, buf).cpu().numpy()
+            assert r.shape[0] == c
+            if c > 1:
+                assert np.all(np.diff(r[:, 0]) >= 0)
+            parts.append(r)
+            total += c
+        assert total == full.shape[0]
+        merged = np.concatenate(parts)
+        merged = merged[np.lexsort(merged.T[::-1])]
+        np.testing.assert_array_equal(merged, full)
+    with pytest.raises(hm.HMError):
+        hm.count_matches_part(G, P, hm.INDUCED, nparts, nparts)
+
+
+def test_instrumented_kernels_agree_and_count_bytes(hm):
+    g = synth.config2_graph(scale=12)
+    G = hm.Graph.from_synth(g)
+    sp = synth.config2_patterns()[1]
+    P = hm.Pattern.from_synth(sp)
+    plain = hm.enumerate_matches(G, P, hm.INDUCED).cpu().numpy()
+    st0 = hm.last_stats()
+    assert st0["bytes_extend"] == 0 and st0["kernel_launches"] >= 3
+    hm.set_counters(True)
+    try:
+        inst = hm.enumerate_matches(G, P, hm.INDUCED).cpu().numpy()
+        st = hm.last_stats()
+    finally:
+        hm.set_counters(False)
+    np.testing.assert_array_equal(inst, plain)
+    assert st["bytes_edge_scan"] >= 12 * g.m
+    assert st["bytes_extend"] > 0 and st["candidates"] > 0
