@@ -201,6 +201,31 @@ hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mod
                              void *stream);
 
 /* ------------------------------------------------------------------------
+ * hm_count_matches_static -- hm_count_matches without any device allocation.
+ * The paper has no counterpart: this is an interface for callers that cannot
+ * allocate device memory while they match, e.g. a process whose device memory
+ * is carved up in advance by another allocator (a framework's caching pool or
+ * a hard per-process budget), or a latency-critical loop in which cudaMalloc,
+ * which may synchronise the whole device, is not acceptable.
+ *   Working memory (control block, donation queue, two seed queues) comes from
+ *   one file-scope device array of HM_STATIC_SCRATCH_BYTES (64 MiB).  Every GPU
+ *   that loads the library holds that array until the process exits.
+ *   The graph may have at most HM_STATIC_MAX_ARCS arcs (one seed slot per
+ *   arc in each seed queue); a larger graph is rejected with HM_ERR_CAPACITY
+ *   before anything is launched.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current) and caches it; make that first call before any stream
+ *   capture.  The call allocates nothing: no cudaMalloc, no cudaFree, no pool.
+ *   All calls on a device share the array, which keeps the previous call's
+ *   contents (the call clears what must start at zero): calls whose work
+ *   overlaps on the GPU, e.g. on two streams, race on it -- serialise them.
+ *   Otherwise as hm_count_matches (same result, same errors). */
+enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3768304 };
+
+hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                  uint64_t *count, void *stream);
+
+/* ------------------------------------------------------------------------
  * Work budget (watchdog).  Every extension kernel stops when either limit is
  * reached and the call returns HM_ERR_BUDGET:
  *   max_ms      wall-clock limit per kernel (0 = default, 120000 ms);

@@ -15,6 +15,7 @@ HM_OK, HM_ERR_ARG, HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_PATTERN = 0, 1, 2, 
 HM_ERR_OOM, HM_ERR_CAPACITY, HM_ERR_BUDGET, HM_ERR_CUDA, HM_ERR_NO_DEVICE = 5, 6, 7, 8, 9
 HM_MONO, HM_INDUCED = 0, 1
 HM_MAX_K = 16
+HM_STATIC_MAX_ARCS = 3768304
 
 #: every function include/hipermotif.h declares
 EXPORTED = [
@@ -23,7 +24,7 @@ EXPORTED = [
     "hm_load_pattern", "hm_free_pattern", "hm_pattern_order", "hm_count_matches",
     "hm_enumerate_matches", "hm_count_matches_rooted", "hm_count_matches_part",
     "hm_enumerate_matches_part", "hm_injected_states", "hm_set_budget",
-    "hm_last_stats", "hm_set_timing", "hm_set_counters",
+    "hm_last_stats", "hm_set_timing", "hm_set_counters", "hm_count_matches_static",
 ]
 
 
@@ -81,6 +82,7 @@ _SIGS = {
     "hm_last_stats": (_st, [ctypes.POINTER(hm_stats)]),
     "hm_set_timing": (_st, [ctypes.c_int]),
     "hm_set_counters": (_st, [ctypes.c_int]),
+    "hm_count_matches_static": (_st, [_vp, _vp, ctypes.c_int, _pu64, _vp]),
 }
 
 

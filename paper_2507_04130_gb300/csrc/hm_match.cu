@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "hm_internal.cuh"
 
@@ -1108,4 +1109,143 @@ extern "C" hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, 
                                         void *stream) {
   return run_match(g, p, mode, -1, nullptr, states_dev, cap, count, (cudaStream_t)stream,
                    Want::kStates);
+}
+
+// ---------------------------------------------------------------------------
+// Counting without any device allocation (hm_count_matches_static).
+//
+// Some callers cannot allocate device memory while they match: a process
+// whose device memory is carved up in advance by another allocator (a
+// framework's caching pool, or a hard per-process budget) and must not take
+// more, or a latency-critical loop where a cudaMalloc, which may synchronise
+// the whole device, is not acceptable.  For them this entry point takes every
+// byte of working memory -- the control block, the donation queue and the two
+// seed queues -- from one file-scope device array of fixed size.  Every GPU
+// that loads the library holds that array until the process exits; every call
+// on a device shares it, so calls whose work overlaps on the GPU (for example
+// on two streams) race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace hm {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
+constexpr size_t kStaticCtlBytes = 256;
+constexpr size_t kStaticQseqBytes = sizeof(unsigned long long) * kQueueCap;
+constexpr size_t kStaticQbufBytes = sizeof(Task) * kQueueCap;
+constexpr size_t kStaticSeedBase = kStaticCtlBytes + kStaticQseqBytes + kStaticQbufBytes;
+// two seed queues of int2, each able to hold one state per target arc
+constexpr int64_t kStaticMaxArcs =
+    (int64_t)((kStaticScratchBytes - kStaticSeedBase) / (2 * sizeof(int2)));
+static_assert(kStaticSeedBase % 256 == 0, "static scratch layout alignment");
+static_assert(kStaticMaxArcs == HM_STATIC_MAX_ARCS, "header constant out of date");
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_lock;
+void *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+hm_status static_scratch(void **out) {
+  int dev = 0;
+  HM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return HM_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_static_lock);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return HM_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return HM_OK;
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mode mode,
+                                             uint64_t *count, void *stream) {
+  using namespace hm;
+  if (!g || !p || !count || (mode != HM_MONO && mode != HM_INDUCED)) return HM_ERR_ARG;
+  if (g->m > kStaticMaxArcs) return HM_ERR_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  void *base = nullptr;
+  hm_status rc = static_scratch(&base);
+  if (rc != HM_OK) return rc;
+  unsigned char *b = static_cast<unsigned char *>(base);
+  Ctl *ctl = reinterpret_cast<Ctl *>(b);
+  unsigned long long *qseq = reinterpret_cast<unsigned long long *>(b + kStaticCtlBytes);
+  Task *qbuf = reinterpret_cast<Task *>(b + kStaticCtlBytes + kStaticQseqBytes);
+  int2 *seeds_a = reinterpret_cast<int2 *>(b + kStaticSeedBase);
+  int2 *seeds_b = seeds_a + kStaticMaxArcs;
+
+  hm_stats &st = tls_stats();
+  std::memset(&st, 0, sizeof(st));
+  const Plan &plan = p->plan[mode];
+  const DevGraph G = g->dev();
+  const int64_t m = g->m;
+  const int sms = num_sms();
+  uint32_t launches = 0;
+  // the array keeps the previous call's contents: clear the control block and the queue
+  HM_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  k_qinit<<<64, 256, 0, s>>>(qseq);
+  ++launches;
+  if (m) {
+    const int64_t groups = (m + 3) / 4;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((groups + kSeedThreads - 1) / kSeedThreads, (int64_t)sms * 8));
+    k_edge_seed<false><<<grid, kSeedThreads, 0, s>>>(G, plan, nullptr, seeds_a,
+                                                     (unsigned long long)kStaticMaxArcs,
+                                                     &ctl->nseeds_raw, &ctl->bytes_edge, 0, m);
+    ++launches;
+  }
+  const int2 *seeds = seeds_a;
+  const unsigned long long *nseeds = &ctl->nseeds_raw;
+  if (plan.ov_need > 0) {
+    k_seed_overlap<false><<<sms * 8, kSeedThreads, 0, s>>>(
+        G, plan.ov_need, seeds_a, &ctl->nseeds_raw, seeds_b, (unsigned long long)kStaticMaxArcs,
+        &ctl->nseeds, &ctl->bytes_overlap);
+    ++launches;
+    seeds = seeds_b;
+    nseeds = &ctl->nseeds;
+  }
+  if (p->k == 2) {
+    k_seed_rows<<<sms * 4, 256, 0, s>>>(plan, seeds, nseeds, nullptr, 0, ctl);
+    ++launches;
+  } else {
+    ExtArgs A{};
+    A.seeds = seeds;
+    A.nseeds = nseeds;
+    A.qbuf = qbuf;
+    A.qseq = qseq;
+    A.ctl = ctl;
+    A.rows = nullptr;
+    A.cap = 0;
+    A.root_mask = nullptr;
+    A.budget_ns = budget_ms() * 1000000ull;
+    A.max_chunks = budget_chunks();
+    const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
+    const int grid = extend_grid(false, false, smem);
+    if (grid <= 0) return HM_ERR_CUDA;
+    extend_kernel(false, false)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    ++launches;
+  }
+  HM_CUDA_TRY(cudaGetLastError());
+  Ctl h;
+  HM_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  HM_CUDA_TRY(cudaStreamSynchronize(s));
+  st.seeds_scanned = (uint64_t)m;
+  st.states_injected = plan.ov_need > 0 ? h.nseeds : h.nseeds_raw;
+  st.tasks_donated = h.donated;
+  st.chunks = h.chunks;
+  st.matches = h.count;
+  st.kernel_launches = launches;
+  if (h.status == kStatBudget) return HM_ERR_BUDGET;
+  if (h.status != kStatOk) return HM_ERR_CUDA;
+  *count = h.count;
+  return HM_OK;
 }
