@@ -220,7 +220,7 @@ hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mod
  *   contents (the call clears what must start at zero): calls whose work
  *   overlaps on the GPU, e.g. on two streams, race on it -- serialise them.
  *   Otherwise as hm_count_matches (same result, same errors). */
-enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3768304 };
+enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3768272 };
 
 hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mode mode,
                                   uint64_t *count, void *stream);
@@ -233,6 +233,39 @@ hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mod
  * Process-wide setting; takes effect for calls that start afterwards.
  * ------------------------------------------------------------------------ */
 hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
+
+/* ------------------------------------------------------------------------
+ * Launch knobs of the extension kernel (process-wide; read by calls that
+ * start afterwards).  None of them changes any result, only speed.
+ *   extend_min_blocks  resident 256-thread blocks per SM the kernel is
+ *                      compiled for: 5 (default), 6 or 8 (fewer registers
+ *                      per thread, more warps to hide load latency).
+ *   split_min          a busy warp donates half of a candidate range to idle
+ *                      warps only while the range holds at least this many
+ *                      candidates (default 64, >= 2).
+ *   pair_mode          1: when a whole candidate range fits one round of
+ *                      (candidate, condition) pairs (candidates x conditions
+ *                      <= 32), one lane per pair, so a candidate's searches
+ *                      run side by side; 0 (default): one lane per candidate,
+ *                      conditions in turn with early exit.
+ *   seeds_per_fetch    depth-2 states a warp claims from the seed queue at
+ *                      once (default 1, at most 1024).
+ *   poll_every         a busy warp looks for idle warps' donation requests
+ *                      every poll_every candidate chunks (a power of two,
+ *                      1..65536, default 128); each request is claimed by
+ *                      exactly one busy warp.
+ * A zero field takes its default.  HM_ERR_ARG for any other value.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t extend_min_blocks;
+  int32_t split_min;
+  int32_t pair_mode;
+  int32_t seeds_per_fetch;
+  int32_t poll_every;
+} hm_tuning;
+
+hm_status hm_set_tuning(const hm_tuning *t);
+hm_status hm_get_tuning(hm_tuning *t);
 
 /* ------------------------------------------------------------------------
  * Statistics of the calling thread's last matching call (host struct).

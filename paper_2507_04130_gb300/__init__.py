@@ -27,7 +27,8 @@ from .binding import HMError, check, lib
 
 __all__ = ["Graph", "Pattern", "count_matches", "enumerate_matches", "count_matches_rooted",
            "count_matches_part", "enumerate_matches_part",
-           "injected_states", "set_budget", "set_timing", "set_counters", "last_stats", "MONO", "INDUCED",
+           "injected_states", "set_budget", "set_timing", "set_counters", "set_tuning", "get_tuning",
+           "last_stats", "MONO", "INDUCED",
            "HMError", "binding"]
 
 
@@ -242,6 +243,20 @@ def set_timing(enabled: bool):
 def set_counters(enabled: bool):
     """Run instrumented kernels that tally algorithmic bytes (measurement only; slower)."""
     check(lib.hm_set_counters(1 if enabled else 0), "hm_set_counters")
+
+
+def set_tuning(extend_min_blocks: int = 0, split_min: int = 0, pair_mode: int = 0,
+               seeds_per_fetch: int = 0, poll_every: int = 0):
+    """Set the extension kernel's launch knobs (0 = default; results never change)."""
+    t = binding.hm_tuning(int(extend_min_blocks), int(split_min), int(pair_mode),
+                          int(seeds_per_fetch), int(poll_every))
+    check(lib.hm_set_tuning(ctypes.byref(t)), "hm_set_tuning")
+
+
+def get_tuning() -> dict:
+    t = binding.hm_tuning()
+    check(lib.hm_get_tuning(ctypes.byref(t)), "hm_get_tuning")
+    return t.as_dict()
 
 
 def last_stats() -> dict:

@@ -15,7 +15,7 @@ HM_OK, HM_ERR_ARG, HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_PATTERN = 0, 1, 2, 
 HM_ERR_OOM, HM_ERR_CAPACITY, HM_ERR_BUDGET, HM_ERR_CUDA, HM_ERR_NO_DEVICE = 5, 6, 7, 8, 9
 HM_MONO, HM_INDUCED = 0, 1
 HM_MAX_K = 16
-HM_STATIC_MAX_ARCS = 3768304
+HM_STATIC_MAX_ARCS = 3768272
 
 #: every function include/hipermotif.h declares
 EXPORTED = [
@@ -25,6 +25,7 @@ EXPORTED = [
     "hm_enumerate_matches", "hm_count_matches_rooted", "hm_count_matches_part",
     "hm_enumerate_matches_part", "hm_injected_states", "hm_set_budget",
     "hm_last_stats", "hm_set_timing", "hm_set_counters", "hm_count_matches_static",
+    "hm_set_tuning", "hm_get_tuning",
 ]
 
 
@@ -47,6 +48,19 @@ class hm_stats(ctypes.Structure):
         ("bytes_overlap", ctypes.c_uint64),
         ("bytes_extend", ctypes.c_uint64),
         ("candidates", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class hm_tuning(ctypes.Structure):
+    _fields_ = [
+        ("extend_min_blocks", ctypes.c_int32),
+        ("split_min", ctypes.c_int32),
+        ("pair_mode", ctypes.c_int32),
+        ("seeds_per_fetch", ctypes.c_int32),
+        ("poll_every", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -83,6 +97,8 @@ _SIGS = {
     "hm_set_timing": (_st, [ctypes.c_int]),
     "hm_set_counters": (_st, [ctypes.c_int]),
     "hm_count_matches_static": (_st, [_vp, _vp, ctypes.c_int, _pu64, _vp]),
+    "hm_set_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
+    "hm_get_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
 }
 
 

@@ -9,6 +9,8 @@ std::atomic<uint64_t> g_budget_ms{120000};
 std::atomic<uint64_t> g_budget_chunks{0};
 std::atomic<int> g_timing{0};
 std::atomic<int> g_counters{0};
+std::atomic<int> g_min_blocks{5}, g_split_min{64}, g_pair_mode{0}, g_seeds_per_fetch{1};
+std::atomic<int> g_poll_every{128};
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -17,6 +19,15 @@ hm_stats &tls_stats() {
 }
 bool timing_enabled() { return g_timing.load(std::memory_order_relaxed) != 0; }
 bool counters_enabled() { return g_counters.load(std::memory_order_relaxed) != 0; }
+hm_tuning tuning() {
+  hm_tuning t{};
+  t.extend_min_blocks = g_min_blocks.load(std::memory_order_relaxed);
+  t.split_min = g_split_min.load(std::memory_order_relaxed);
+  t.pair_mode = g_pair_mode.load(std::memory_order_relaxed);
+  t.seeds_per_fetch = g_seeds_per_fetch.load(std::memory_order_relaxed);
+  t.poll_every = g_poll_every.load(std::memory_order_relaxed);
+  return t;
+}
 uint64_t budget_ms() { return g_budget_ms.load(std::memory_order_relaxed); }
 uint64_t budget_chunks() { return g_budget_chunks.load(std::memory_order_relaxed); }
 }  // namespace hm
@@ -56,5 +67,28 @@ extern "C" hm_status hm_set_timing(int enabled) {
 
 extern "C" hm_status hm_set_counters(int enabled) {
   hm::g_counters.store(enabled ? 1 : 0);
+  return HM_OK;
+}
+
+extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
+  if (!t) return HM_ERR_ARG;
+  const int mb = t->extend_min_blocks ? t->extend_min_blocks : 5;
+  const int sm = t->split_min ? t->split_min : 64;
+  const int sp = t->seeds_per_fetch ? t->seeds_per_fetch : 1;
+  const int pe = t->poll_every ? t->poll_every : 128;
+  if ((mb != 5 && mb != 6 && mb != 8) || sm < 2 || sp < 1 || sp > 1024 ||
+      (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)))
+    return HM_ERR_ARG;
+  hm::g_min_blocks.store(mb);
+  hm::g_split_min.store(sm);
+  hm::g_pair_mode.store(t->pair_mode);
+  hm::g_seeds_per_fetch.store(sp);
+  hm::g_poll_every.store(pe);
+  return HM_OK;
+}
+
+extern "C" hm_status hm_get_tuning(hm_tuning *t) {
+  if (!t) return HM_ERR_ARG;
+  *t = hm::tuning();
   return HM_OK;
 }

@@ -90,6 +90,14 @@ enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 
+// Lists of at most this many entries are compared with independent loads (one
+// round trip to the cache) instead of being halved one dependent probe at a
+// time; 0 = plain binary search to the end.
+#ifndef HM_SCAN_TAIL
+#define HM_SCAN_TAIL 0
+#endif
+constexpr int kScanTail = HM_SCAN_TAIL;
+
 // First index i in the sorted list a[lo, lo+len) with a[i] >= x (lo+len if none).
 __device__ __forceinline__ int64_t lower_bound_idx(const int32_t *__restrict__ a, int64_t lo,
                                                    int64_t len, int32_t x) {
@@ -106,34 +114,55 @@ __device__ __forceinline__ int64_t lower_bound_idx(const int32_t *__restrict__ a
   return lo;
 }
 
-// Is x in a[lo, lo+len)?  Returns its index or -1.
-__device__ __forceinline__ int64_t search(const int32_t *__restrict__ a, int64_t lo, int64_t len,
-                                          int32_t x) {
-  int64_t end = lo + len;
-  int64_t i = lower_bound_idx(a, lo, len, x);
-  return (i < end && __ldg(a + i) == x) ? i : -1;
-}
-
-// search() that also adds the bytes it reads to `bytes` when kCount is set
-// (the algorithmic-byte counters of an instrumented launch).
+// Is x in the sorted list a[lo, lo+len)?  Returns its index or -1.  Halves the
+// range while it is longer than kScanTail, then compares the rest at once.
 template <bool kCount>
 __device__ __forceinline__ int64_t search_c(const int32_t *__restrict__ a, int64_t lo, int64_t len,
                                             int32_t x, uint64_t &bytes) {
-  const int64_t end = lo + len;
-  while (len > 0) {
-    int64_t half = len >> 1;
-    int32_t v = __ldg(a + lo + half);
+  if (kScanTail == 0) {
+    const int64_t end = lo + len;
+    while (len > 0) {
+      const int64_t half = len >> 1;
+      const int32_t v = __ldg(a + lo + half);
+      if (kCount) bytes += 4;
+      if (v < x) {
+        lo += half + 1;
+        len -= half + 1;
+      } else {
+        len = half;
+      }
+    }
+    if (lo >= end) return -1;
+    if (kCount) bytes += 4;
+    return __ldg(a + lo) == x ? lo : -1;
+  }
+  while (len > kScanTail) {
+    const int64_t half = len >> 1;
+    const int32_t v = __ldg(a + lo + half);
     if (kCount) bytes += 4;
     if (v < x) {
       lo += half + 1;
       len -= half + 1;
     } else {
-      len = half;
+      len = half + 1;  // keep a[lo + half] (it may equal x)
     }
   }
-  if (lo >= end) return -1;
-  if (kCount) bytes += 4;
-  return __ldg(a + lo) == x ? lo : -1;
+  constexpr int kT = kScanTail > 0 ? kScanTail : 1;
+  int32_t v[kT];
+#pragma unroll
+  for (int i = 0; i < kT; ++i) v[i] = i < len ? __ldg(a + lo + i) : 0;
+  if (kCount) bytes += 4 * (uint64_t)len;
+  int64_t hit = -1;
+#pragma unroll
+  for (int i = kT - 1; i >= 0; --i)
+    if (i < len && v[i] == x) hit = lo + i;
+  return hit;
+}
+
+__device__ __forceinline__ int64_t search(const int32_t *__restrict__ a, int64_t lo, int64_t len,
+                                          int32_t x) {
+  uint64_t unused = 0;
+  return search_c<false>(a, lo, len, x, unused);
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -184,6 +213,7 @@ namespace hm {
 hm_stats &tls_stats();
 bool timing_enabled();
 bool counters_enabled();
+hm_tuning tuning();  // current process-wide extension knobs (validated)
 uint64_t budget_ms();
 uint64_t budget_chunks();
 

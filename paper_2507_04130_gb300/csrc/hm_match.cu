@@ -35,6 +35,12 @@
 
 #include "hm_internal.cuh"
 
+// 1: load a candidate's offsets together with its label/degree record;
+// 0: only after it passes the degree filter.
+#ifndef HM_EAGER_OFFSETS
+#define HM_EAGER_OFFSETS 0
+#endif
+
 namespace hm {
 
 void ensure_pool();
@@ -58,26 +64,33 @@ struct Task {
 static_assert(sizeof(Task) == 96, "task layout");
 constexpr int kTaskWords = sizeof(Task) / 4;
 
+// Control block of one call.  Words that different warps hit at high rates
+// sit on separate 128-byte lines so they do not contend for one cache line.
 struct Ctl {
-  unsigned long long nseeds_raw;  // arcs passing the edge scan
-  unsigned long long nseeds;      // after the overlap test
-  unsigned long long seed_next;
-  unsigned long long head, tail;
+  alignas(128) unsigned long long seed_next;  // next unclaimed seed
+  alignas(128) unsigned long long head;       // donation queue
+  unsigned long long tail;
+  alignas(128) int32_t active;                // warps that hold work
+  alignas(128) int32_t hungry;                // warps waiting for work
+  int32_t requests;                           // donations asked for, not yet claimed
+  alignas(128) int32_t status;
+  alignas(128) unsigned long long nseeds_raw; // arcs passing the edge scan
+  unsigned long long nseeds;                  // after the overlap test
   unsigned long long count;
   unsigned long long rows_written;
   unsigned long long chunks;
   unsigned long long donated;
-  unsigned long long bytes_edge;     // algorithmic bytes (instrumented launches only)
+  unsigned long long bytes_edge;              // algorithmic bytes (instrumented launches only)
   unsigned long long bytes_overlap;
   unsigned long long bytes_extend;
-  unsigned long long lanes;          // candidates examined (instrumented launches only)
-  int32_t active;
-  int32_t hungry;
-  int32_t status;
-  int32_t pad;
+  unsigned long long lanes;                   // candidates examined (instrumented launches only)
 };
 
 struct ExtArgs {
+  int32_t split_min;        // donate a range only while it holds at least this many candidates
+  int32_t pair_mode;        // spread (candidate, condition) pairs over lanes on short ranges
+  int32_t seeds_per_fetch;  // seeds a warp claims at once
+  uint32_t poll_mask;       // a busy warp looks for donation requests every poll_mask+1 chunks
   const int2 *seeds;
   const unsigned long long *nseeds;
   Task *qbuf;
@@ -409,11 +422,19 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
   int4 vi = make_int4(0, 0, 0, 0);
   longlong2 oc = make_longlong2(0, 0);
   if (need_c) {
+#if HM_EAGER_OFFSETS
+    // both records in flight together (the offsets are used by most searches)
+    if (kC) ctr += nc > 1 ? 32 : 16;
+    vi = __ldg(&G.vi[c]);
+    if (nc > 1) oc = __ldg(&G.off[c]);
+    if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
+#else
     if (kC) ctr += 16;
     vi = __ldg(&G.vi[c]);
     if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
     if (kC && nc > 1) ctr += 16;
     if (nc > 1) oc = __ldg(&G.off[c]);
+#endif
   }
   for (int j = 0; j < nc; ++j) {
     if (j == drive) continue;
@@ -451,6 +472,51 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
     }
   }
   return true;
+}
+
+// One condition j of position p on candidate c (the j-th entry of cons[p]).
+// The lane with `base` set also applies the per-candidate checks
+// (injectivity, root mask, degree filter on inner levels).
+template <bool kC>
+__device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, const WarpState &S,
+                                          const int2 *__restrict__ grp, int p, int j, int32_t c,
+                                          bool base, bool leaf, const uint8_t *root_mask,
+                                          uint64_t &ctr) {
+  if (base) {
+    for (int i = 0; i < p; ++i)
+      if (S.map[i] == c) return false;
+    if (root_mask && p == P.root_pos && !root_mask[c]) return false;
+  }
+  if (kC) ctr += 16;
+  const int4 vi = __ldg(&G.vi[c]);
+  if (base && !leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
+  const Cons cs = P.cons[p][j];
+  const int q = cs.q;
+  const int32_t fq = S.map[q];
+  const bool fwd = cs.kind == kOut || cs.kind == kNotOut;
+  if (cs.kind <= kIn) {
+    const int2 r = grp[P.gbase[p] + j];
+    const int32_t rev_len = fwd ? vi.z : vi.y;
+    if (r.y == 0 || rev_len == 0) return false;
+    if (rev_len < r.y) {
+      if (kC) ctr += 16;
+      const longlong2 oc = __ldg(&G.off[c]);
+      const int64_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
+                            : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
+      if (kC && i >= 0) ctr += 4;
+      return i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+    }
+    const int64_t lo = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
+    return search_c<kC>(fwd ? G.gout_adj : G.gin_adj, lo, r.y, c, ctr) >= 0;
+  }
+  const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
+  const int32_t lb = fwd ? vi.z : vi.y;
+  if (la == 0 || lb == 0) return true;
+  if (la <= lb)
+    return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
+  if (kC) ctr += 16;
+  const longlong2 oc = __ldg(&G.off[c]);
+  return search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) < 0;
 }
 
 // ---- bounded lock-free queue (Vyukov-style sequence numbers) --------------
@@ -532,14 +598,17 @@ __device__ __forceinline__ bool queue_maybe_nonempty(const ExtArgs &A) {
 }
 
 // Split the shallowest unfinished range (or pending chunk) and donate one part.
-__device__ void try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0, int level,
-                           int lane) {
+// The task being run may restrict its first chunk [first_lo, first_lo + 32) at
+// depth L0 to the candidates in first_mask; a split of that window hands the
+// shifted restriction to the new task (such tasks never extend past the window).
+__device__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0, int level,
+                           int lane, int64_t first_lo, uint32_t first_mask) {
   int l = -1, kind = 0;
   for (int d = L0; d <= level; ++d) {
-    if (S.hi[d] - S.lo[d] >= 64) { l = d; kind = 0; break; }
+    if (S.hi[d] - S.lo[d] >= A.split_min) { l = d; kind = 0; break; }
     if (d < level && __popc(S.mask[d]) >= 2) { l = d; kind = 1; break; }
   }
-  if (l < 0) return;
+  if (l < 0) return false;
   if (lane == 0) {
     Task &t = S.stage;
     t.depth = l;
@@ -551,6 +620,8 @@ __device__ void try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0
       t.lo = mid;
       t.hi = S.hi[l];
       t.pmask = kFull;
+      if (l == L0 && first_mask != kFull && mid >= first_lo && mid < first_lo + 32)
+        t.pmask = first_mask >> (mid - first_lo);
     } else {
       uint32_t m = S.mask[l];
       int keep = __popc(m) >> 1;
@@ -577,14 +648,15 @@ __device__ void try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0
     }
   }
   __syncwarp();
+  return pushed;
 }
 
 __host__ __device__ constexpr size_t warp_smem_bytes(int ngrp) {
   return (sizeof(WarpState) + sizeof(int2) * (size_t)ngrp + 15) / 16 * 16;
 }
 
-template <bool kRows, bool kC>
-__global__ void __launch_bounds__(kExtThreads)
+template <bool kRows, bool kC, int kMinBlocks>
+__global__ void __launch_bounds__(kExtThreads, kMinBlocks)
 k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
          const __grid_constant__ ExtArgs A) {
   uint64_t ctr = 0, lanes = 0;
@@ -597,6 +669,8 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
   const unsigned long long deadline = globaltimer_ns() + A.budget_ns;
   const unsigned long long nseeds = *A.nseeds;
   unsigned long long my_count = 0, my_chunks = 0;
+  unsigned long long seed_at = 0, seed_end = 0;  // this warp's claimed seeds
+  int32_t requests_seen = 0, status_seen = kStatOk;  // lane 0: values from the previous poll
   bool seeds_done = false, stop = false;
   if (lane == 0) atomicAdd(&A.ctl->active, 1);
 
@@ -604,10 +678,14 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     // ---------------- acquire a task ----------------
     int got = 0;  // 1 seed, 2 donated
     if (!seeds_done) {
-      unsigned long long s = 0;
-      if (lane == 0) s = atomicAdd(&A.ctl->seed_next, 1ull);
-      s = __shfl_sync(kFull, s, 0);
-      if (s < nseeds) {
+      if (seed_at >= seed_end) {
+        unsigned long long s0 = 0;
+        if (lane == 0) s0 = atomicAdd(&A.ctl->seed_next, (unsigned long long)A.seeds_per_fetch);
+        seed_at = __shfl_sync(kFull, s0, 0);
+        seed_end = min(seed_at + (unsigned long long)A.seeds_per_fetch, nseeds);
+      }
+      const unsigned long long s = seed_at++;
+      if (s < seed_end) {
         const int2 uv = A.seeds[s];
         if (kC && lane == 0) ctr += 8;
         set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
@@ -624,6 +702,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
       // go idle: advertise, and wait for a donation or for global quiescence
       if (lane == 0) {
         atomicAdd(&A.ctl->hungry, 1);
+        atomicAdd(&A.ctl->requests, 1);
         atomicSub(&A.ctl->active, 1);
       }
       unsigned ns = 64;
@@ -698,57 +777,100 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
         }
         ++my_chunks;
         if ((my_chunks & 63) == 0) {
+          // budget check; the status word read here was requested 64 chunks
+          // ago, so its latency is hidden behind that work
           int halt = 0;
           if (lane == 0) {
-            if (ld_volatile(&A.ctl->status) != kStatOk) halt = 1;
+            const int32_t status = status_seen;
+            status_seen = ld_volatile(&A.ctl->status);
+            if (status != kStatOk) halt = 1;
             else if (globaltimer_ns() > deadline) {
               atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
               halt = 1;
-            } else {
+            } else if (A.max_chunks) {
               unsigned long long tot = atomicAdd(&A.ctl->chunks, 64ull) + 64;
-              if (A.max_chunks && tot > A.max_chunks) {
+              if (tot > A.max_chunks) {
                 atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
                 halt = 1;
               }
+            } else {
+              atomicAdd(&A.ctl->chunks, 64ull);
             }
           }
           if (__shfl_sync(kFull, halt, 0)) { stop = true; break; }
         }
-        if (level < k - 1 || (my_chunks & 7) == 0) {
-          // donate only while fewer tasks wait in the queue than warps wait for work
+        if ((my_chunks & A.poll_mask) == 0) {
+          // donate only while fewer tasks wait in the queue than warps wait
+          // for work; the idle-warp count used is the one requested at the
+          // previous poll, so the poll does not stall the warp
           int want = 0;
           if (lane == 0) {
-            int32_t hungry = ld_volatile(&A.ctl->hungry);
-            if (hungry > 0) {
-              atomic_u64 head(A.ctl->head), tail(A.ctl->tail);
-              unsigned long long queued = tail.load(cuda::memory_order_relaxed) -
-                                          head.load(cuda::memory_order_relaxed);
-              want = queued < (unsigned long long)hungry;
-            }
+            const int32_t asked = requests_seen;
+            requests_seen = ld_volatile(&A.ctl->requests);
+            // claim one outstanding request: one donation per idle warp's ask
+            if (asked > 0) want = atomicSub(&A.ctl->requests, 1) > 0 ? 1 : 2;
           }
-          if (__shfl_sync(kFull, want, 0)) {
-            try_donate(A, P, S, L0, level, lane);
-            hi = S.hi[level];  // a split of this level keeps [lo, mid)
+          want = __shfl_sync(kFull, want, 0);
+          if (want) {
+            bool gave = false;
+            if (want == 1) {
+              gave = try_donate(A, P, S, L0, level, lane, first_lo, first_mask);
+              hi = S.hi[level];  // a split of this level keeps [lo, mid)
+            }
+            if (lane == 0 && !gave) atomicAdd(&A.ctl->requests, 1);  // not claimed / nothing to give
           }
         }
         const int drive = S.drive[level];
         const Cons dc = P.cons[level][drive];
         const int32_t *adj = dc.kind == kOut ? G.gout_adj : G.gin_adj;
-        const uint32_t allow = (level == L0 && lo == first_lo) ? first_mask : kFull;
-        const int64_t idx = lo + lane;
+        uint32_t allow = kFull;
+        if (level == L0 && first_mask != kFull && lo >= first_lo && lo < first_lo + 32)
+          allow = first_mask >> (lo - first_lo);
+        const bool leaf = level == k - 1;
+        const int J = P.ncons[level] - 1;  // conditions besides the driving one
         bool ok = false;
         int32_t c = -1;
-        if (idx < hi && ((allow >> lane) & 1u)) {
-          c = __ldg(adj + idx);
-          if (kC) {
-            ctr += 4;
-            ++lanes;
+        uint32_t m;
+        int take;
+        if (A.pair_mode && J >= 2 && (hi - lo) * J <= 32) {
+          // the whole range fits one round of (candidate, condition) pairs:
+          // a candidate's searches run side by side instead of one after another
+          take = (int)(hi - lo);
+          const int ci = lane / J, slot = lane - ci * J;
+          bool pass = false;
+          if (ci < take && ((allow >> ci) & 1u)) {
+            const int32_t cc = __ldg(adj + lo + ci);
+            if (kC && slot == 0) {
+              ctr += 4;
+              ++lanes;
+            }
+            pass = check_one<kC>(G, P, S, grp, level, slot < drive ? slot : slot + 1, cc, slot == 0,
+                                 leaf, A.root_mask, ctr);
           }
-          ok = check_candidate<kC>(G, P, S, grp, level, drive, c, level == k - 1, A.root_mask, ctr);
+          const uint32_t bal = __ballot_sync(kFull, pass);
+          const uint32_t need = (1u << J) - 1u;
+          m = 0;
+          for (int i = 0; i < take; ++i)
+            if (((bal >> (i * J)) & need) == need) m |= 1u << i;
+          if (lane < take && ((m >> lane) & 1u)) {
+            ok = true;
+            c = __ldg(adj + lo + lane);
+          }
+        } else {
+          take = 32;
+          const int64_t idx = lo + lane;
+          if (idx < hi && ((allow >> lane) & 1u)) {
+            c = __ldg(adj + idx);
+            if (kC) {
+              ctr += 4;
+              ++lanes;
+            }
+            ok = check_candidate<kC>(G, P, S, grp, level, drive, c, leaf, A.root_mask, ctr);
+          }
+          m = __ballot_sync(kFull, ok);
         }
-        const uint32_t m = __ballot_sync(kFull, ok);
-        if (lane == 0) S.lo[level] = lo + 32;
-        if (level == k - 1) {
+        if (lane == 0) S.lo[level] = lo + take;
+        if (leaf) {
           // leaf: every survivor is a match
           const int nm = __popc(m);
           my_count += nm;
@@ -880,20 +1002,39 @@ struct Scratch {
 
 using ExtendKernel = void (*)(DevGraph, Plan, ExtArgs);
 
-ExtendKernel extend_kernel(bool rows, bool counters) {
-  if (rows) return counters ? k_extend<true, true> : k_extend<true, false>;
-  return counters ? k_extend<false, true> : k_extend<false, false>;
+// Occupancy variants: resident 256-thread blocks per SM requested from the
+// compiler (it caps registers per thread accordingly).
+constexpr int kMinBlockChoices[3] = {5, 6, 8};
+
+int min_blocks_slot(int min_blocks) {
+  for (int i = 0; i < 3; ++i)
+    if (kMinBlockChoices[i] == min_blocks) return i;
+  return 0;
+}
+
+template <bool R, bool C>
+ExtendKernel extend_kernel_mb(int slot) {
+  switch (slot) {
+    case 1: return k_extend<R, C, 6>;
+    case 2: return k_extend<R, C, 8>;
+    default: return k_extend<R, C, 5>;
+  }
+}
+
+ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0) {
+  if (rows) return counters ? extend_kernel_mb<true, true>(slot) : extend_kernel_mb<true, false>(slot);
+  return counters ? extend_kernel_mb<false, true>(slot) : extend_kernel_mb<false, false>(slot);
 }
 
 // Resident blocks of an extension kernel variant for a dynamic shared-memory size.
-int extend_grid(bool rows, bool counters, size_t smem) {
-  static int cache[4][64] = {};
-  const int slot = (int)std::min<size_t>(smem / 1024, 63);
-  int &c = cache[(rows ? 2 : 0) + (counters ? 1 : 0)][slot];
+int extend_grid(bool rows, bool counters, size_t smem, int slot = 0) {
+  static int cache[3][4][64] = {};
+  const int sm = (int)std::min<size_t>(smem / 1024, 63);
+  int &c = cache[slot][(rows ? 2 : 0) + (counters ? 1 : 0)][sm];
   if (!c) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, extend_kernel(rows, counters), kExtThreads, smem);
+        &per_sm, extend_kernel(rows, counters, slot), kExtThreads, smem);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       return 0;
@@ -1016,12 +1157,18 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.root_mask = root_mask;
     A.budget_ns = budget_ms() * 1000000ull;
     A.max_chunks = budget_chunks();
+    const hm_tuning tu = tuning();
+    A.split_min = tu.split_min;
+    A.pair_mode = tu.pair_mode;
+    A.seeds_per_fetch = tu.seeds_per_fetch;
+    A.poll_mask = (uint32_t)tu.poll_every - 1u;
+    const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
-    const int grid = extend_grid(rows, counters, smem);
+    const int grid = extend_grid(rows, counters, smem, slot);
     if (grid <= 0) return HM_ERR_CUDA;
     st.extend_grid = grid;
     st.extend_block = kExtThreads;
-    extend_kernel(rows, counters)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    extend_kernel(rows, counters, slot)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
     ++launches;
     t_ext.stop();
     HM_CUDA_TRY(cudaGetLastError());
@@ -1055,7 +1202,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     for (int i = 0; i < p->k; ++i) cols[i] = i;
     const int sort_cols = p->k;
     hm_status r = radix_sort_rows(out, tmp, (int64_t)h.count, p->k, cols, sort_cols, bits_for(g->n), s);
-    st.kernel_launches += 3 * ((sort_cols * bits_for(g->n) + 7) / 8);
+    st.kernel_launches += 5 * ((sort_cols * bits_for(g->n) + 7) / 8);
     t.stop();
     if (r != HM_OK) return r;
     if (timing) {
@@ -1129,7 +1276,7 @@ namespace hm {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
-constexpr size_t kStaticCtlBytes = 256;
+constexpr size_t kStaticCtlBytes = (sizeof(Ctl) + 255) / 256 * 256;
 constexpr size_t kStaticQseqBytes = sizeof(unsigned long long) * kQueueCap;
 constexpr size_t kStaticQbufBytes = sizeof(Task) * kQueueCap;
 constexpr size_t kStaticSeedBase = kStaticCtlBytes + kStaticQseqBytes + kStaticQbufBytes;
@@ -1228,10 +1375,16 @@ extern "C" hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern
     A.root_mask = nullptr;
     A.budget_ns = budget_ms() * 1000000ull;
     A.max_chunks = budget_chunks();
+    const hm_tuning tu = tuning();
+    A.split_min = tu.split_min;
+    A.pair_mode = tu.pair_mode;
+    A.seeds_per_fetch = tu.seeds_per_fetch;
+    A.poll_mask = (uint32_t)tu.poll_every - 1u;
+    const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
-    const int grid = extend_grid(false, false, smem);
+    const int grid = extend_grid(false, false, smem, slot);
     if (grid <= 0) return HM_ERR_CUDA;
-    extend_kernel(false, false)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    extend_kernel(false, false, slot)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
     ++launches;
   }
   HM_CUDA_TRY(cudaGetLastError());

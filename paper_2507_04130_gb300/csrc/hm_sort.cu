@@ -337,13 +337,19 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
   per_block = (per_block + kTile - 1) / kTile * kTile;
   grid = (int)((nrows + per_block - 1) / per_block);
   uint32_t *hist = nullptr;
-  HM_CUDA_TRY(cudaMallocAsync(&hist, sizeof(uint32_t) * kRadix * grid, stream));
+  const int64_t nhist = (int64_t)kRadix * grid;
+  const int64_t tiles = (nhist + kScanTile - 1) / kScanTile;
+  HM_CUDA_TRY(cudaMallocAsync(&hist, sizeof(uint32_t) * (size_t)(2 * nhist + tiles), stream));
+  uint32_t *starts = hist + nhist, *sums = starts + nhist;
   int32_t *a = rows, *b = tmp;
   for (int p = 0; p < passes; ++p) {
     ks.shift = p * 8;
     k_hist<<<grid, kSortThreads, 0, stream>>>(a, nrows, width, per_block, ks, hist, grid);
-    k_scan<<<1, 1024, 0, stream>>>(hist, (int64_t)kRadix * grid);
-    scatter(a, b, nrows, per_block, ks, hist, grid, stream);
+    // exclusive scan of the (digit, block) counts over many blocks
+    k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, stream>>>(hist, nhist, sums);
+    k_scan<<<1, 1024, 0, stream>>>(sums, tiles);
+    k_tile_scan<<<(unsigned)tiles, kScanThreads, 0, stream>>>(hist, nhist, sums, starts);
+    scatter(a, b, nrows, per_block, ks, starts, grid, stream);
     std::swap(a, b);
   }
   if (a != rows)

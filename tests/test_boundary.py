@@ -102,3 +102,23 @@ def test_graph_load_rejects_bad_arguments_before_the_device(hm):
         hm.binding.HM_ERR_ARG
     assert hm.lib.hm_load_graph(3, 2, None, None, None, None, 0, None, ctypes.byref(h)) == \
         hm.binding.HM_ERR_ARG
+
+
+@pytest.mark.parametrize("bad", [dict(extend_min_blocks=7), dict(split_min=1), dict(pair_mode=2),
+                                 dict(seeds_per_fetch=5000), dict(poll_every=3),
+                                 dict(poll_every=1 << 17)])
+def test_tuning_rejects_bad_values(hm, bad):
+    before = hm.get_tuning()
+    with pytest.raises(hm.HMError) as ei:
+        hm.set_tuning(**bad)
+    assert ei.value.status == hm.binding.HM_ERR_ARG
+    assert hm.get_tuning() == before
+
+
+def test_tuning_defaults_roundtrip(hm):
+    hm.set_tuning(extend_min_blocks=6, split_min=128, pair_mode=1, seeds_per_fetch=4, poll_every=8)
+    assert hm.get_tuning() == dict(extend_min_blocks=6, split_min=128, pair_mode=1, seeds_per_fetch=4,
+                                   poll_every=8)
+    hm.set_tuning()
+    assert hm.get_tuning() == dict(extend_min_blocks=5, split_min=64, pair_mode=0, seeds_per_fetch=1,
+                                   poll_every=128)

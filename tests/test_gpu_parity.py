@@ -378,3 +378,25 @@ def test_instrumented_kernels_agree_and_count_bytes(hm):
     np.testing.assert_array_equal(inst, plain)
     assert st["bytes_edge_scan"] >= 12 * g.m
     assert st["bytes_extend"] > 0 and st["candidates"] > 0
+
+
+@pytest.mark.parametrize("knobs", [dict(extend_min_blocks=6), dict(extend_min_blocks=8),
+                                   dict(pair_mode=1), dict(split_min=2, seeds_per_fetch=7),
+                                   dict(pair_mode=1, split_min=2, poll_every=1),
+                                   dict(poll_every=65536),
+                                   dict(split_min=1000, seeds_per_fetch=64)])
+def test_tuning_knobs_never_change_results(hm, knobs):
+    g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
+    g = synth.Graph(g0.n, g0.src, g0.dst, (g0.vlab % 2).astype(np.int32), g0.elab % 2)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    rng = np.random.default_rng(17)
+    pats = [synth.random_pattern(rng, int(rng.integers(3, 6)), 0.5, n_vlab=2, n_elab=2)
+            for _ in range(4)]
+    hm.set_tuning(**knobs)
+    try:
+        for sp in pats:
+            _check(hm, G, og, sp, oracle.INDUCED)
+            _check(hm, G, og, sp, oracle.MONO, rows=False)
+    finally:
+        hm.set_tuning()
