@@ -149,12 +149,12 @@ __global__ void k_zero_off(int64_t *__restrict__ off, int32_t n) {
 __global__ void k_vertex(const int32_t *__restrict__ vlab, const int64_t *__restrict__ out_off,
                          const int64_t *__restrict__ in_off, const uint32_t *__restrict__ oidx,
                          const uint32_t *__restrict__ iidx, int32_t n, int4 *__restrict__ vi,
-                         longlong2 *__restrict__ voff, int4 *__restrict__ vdir) {
+                         int2 *__restrict__ voff, int4 *__restrict__ vdir) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     int64_t o0 = out_off[v], o1 = out_off[v + 1], i0 = in_off[v], i1 = in_off[v + 1];
     vi[v] = make_int4(vlab[v], (int32_t)(o1 - o0), (int32_t)(i1 - i0), 0);
-    voff[v] = make_longlong2(o0, i0);
+    voff[v] = make_int2((int32_t)o0, (int32_t)i0);
     uint32_t os = oidx ? oidx[o0] : 0, oe = oidx ? oidx[o1] : 0;
     uint32_t is = iidx ? iidx[i0] : 0, ie = iidx ? iidx[i1] : 0;
     vdir[v] = make_int4((int32_t)os, (int32_t)(oe - os), (int32_t)is, (int32_t)(ie - is));
@@ -339,7 +339,7 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
   HM_CUDA_TRY(cudaStreamSynchronize(s));
   HM_CUDA_TRY(cudaGetLastError());
   if (h_err & kErrDup) return HM_ERR_DUP_EDGE;
-  g->bytes = sizeof(int32_t) * 7 * (size_t)m + (sizeof(int4) * 2 + sizeof(longlong2)) * (size_t)n +
+  g->bytes = sizeof(int32_t) * 7 * (size_t)m + (sizeof(int4) * 2 + sizeof(int2)) * (size_t)n +
              sizeof(int4) * (size_t)(g->ndir_out + g->ndir_in);
   return HM_OK;
 }
@@ -410,9 +410,9 @@ extern "C" hm_status hm_graph_export(const hm_graph *g, int64_t *out_off, int32_
   if (in_adj && m) HM_CUDA_TRY(cudaMemcpy(in_adj, g->in_adj, 4 * m, cudaMemcpyDeviceToHost));
   if (in_elab && m) HM_CUDA_TRY(cudaMemcpy(in_elab, g->in_elab, 4 * m, cudaMemcpyDeviceToHost));
   if (out_off || in_off) {
-    longlong2 *h = (longlong2 *)malloc(sizeof(longlong2) * (n ? n : 1));
+    int2 *h = (int2 *)malloc(sizeof(int2) * (n ? n : 1));
     if (!h) return HM_ERR_OOM;
-    cudaError_t e = n ? cudaMemcpy(h, g->off, sizeof(longlong2) * n, cudaMemcpyDeviceToHost)
+    cudaError_t e = n ? cudaMemcpy(h, g->off, sizeof(int2) * n, cudaMemcpyDeviceToHost)
                       : cudaSuccess;
     if (e != cudaSuccess) {
       free(h);

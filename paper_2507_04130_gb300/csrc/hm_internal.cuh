@@ -8,7 +8,7 @@
 //   in_adj   int32[m]  in-neighbours, sorted within each vertex (CSC)
 //   in_elab  int32[m]  label of each in-arc, parallel to in_adj
 //   vi       int4[n]   {vertex label, out-degree, in-degree, 0}
-//   off      longlong2[n] {first out-arc, first in-arc}
+//   off      int2[n]   {first out-arc, first in-arc}   (m < 2^31, so 32-bit offsets)
 // A vertex's label and both degrees arrive in one 16-byte load; its list
 // offsets in a second one, fetched only when a list is actually searched.
 #pragma once
@@ -33,7 +33,7 @@ struct DevGraph {
   const int32_t *in_adj;
   const int32_t *in_elab;
   const int4 *vi;
-  const longlong2 *off;
+  const int2 *off;
   // label-grouped copies of the lists: each vertex's list ordered by
   // (arc label, neighbour label, neighbour id); one directory entry per group
   const int32_t *gout_adj;
@@ -98,31 +98,16 @@ enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
 #endif
 constexpr int kScanTail = HM_SCAN_TAIL;
 
-// First index i in the sorted list a[lo, lo+len) with a[i] >= x (lo+len if none).
-__device__ __forceinline__ int64_t lower_bound_idx(const int32_t *__restrict__ a, int64_t lo,
-                                                   int64_t len, int32_t x) {
-  while (len > 0) {
-    int64_t half = len >> 1;
-    int32_t v = __ldg(a + lo + half);
-    if (v < x) {
-      lo += half + 1;
-      len -= half + 1;
-    } else {
-      len = half;
-    }
-  }
-  return lo;
-}
-
-// Is x in the sorted list a[lo, lo+len)?  Returns its index or -1.  Halves the
-// range while it is longer than kScanTail, then compares the rest at once.
+// Is x in the sorted list a[lo, lo+len)?  Returns its index or -1.  Offsets are
+// 32-bit (the loader caps m below 2^31).  Halves the range while it is longer
+// than kScanTail, then compares the rest at once.
 template <bool kCount>
-__device__ __forceinline__ int64_t search_c(const int32_t *__restrict__ a, int64_t lo, int64_t len,
+__device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32_t lo, int32_t len,
                                             int32_t x, uint64_t &bytes) {
-  if (kScanTail == 0) {
-    const int64_t end = lo + len;
+  if constexpr (kScanTail == 0) {
+    const int32_t end = lo + len;
     while (len > 0) {
-      const int64_t half = len >> 1;
+      const int32_t half = len >> 1;
       const int32_t v = __ldg(a + lo + half);
       if (kCount) bytes += 4;
       if (v < x) {
@@ -135,9 +120,9 @@ __device__ __forceinline__ int64_t search_c(const int32_t *__restrict__ a, int64
     if (lo >= end) return -1;
     if (kCount) bytes += 4;
     return __ldg(a + lo) == x ? lo : -1;
-  }
+  } else {
   while (len > kScanTail) {
-    const int64_t half = len >> 1;
+    const int32_t half = len >> 1;
     const int32_t v = __ldg(a + lo + half);
     if (kCount) bytes += 4;
     if (v < x) {
@@ -152,14 +137,15 @@ __device__ __forceinline__ int64_t search_c(const int32_t *__restrict__ a, int64
 #pragma unroll
   for (int i = 0; i < kT; ++i) v[i] = i < len ? __ldg(a + lo + i) : 0;
   if (kCount) bytes += 4 * (uint64_t)len;
-  int64_t hit = -1;
+  int32_t hit = -1;
 #pragma unroll
   for (int i = kT - 1; i >= 0; --i)
     if (i < len && v[i] == x) hit = lo + i;
   return hit;
+  }
 }
 
-__device__ __forceinline__ int64_t search(const int32_t *__restrict__ a, int64_t lo, int64_t len,
+__device__ __forceinline__ int32_t search(const int32_t *__restrict__ a, int32_t lo, int32_t len,
                                           int32_t x) {
   uint64_t unused = 0;
   return search_c<false>(a, lo, len, x, unused);
@@ -190,7 +176,7 @@ struct hm_graph {
   int64_t m;
   int32_t *src, *out_adj, *out_elab, *in_adj, *in_elab;
   int4 *vi;
-  longlong2 *off;
+  int2 *off;
   int32_t *gout_adj, *gin_adj;
   int4 *gdir_out, *gdir_in, *vdir;
   int64_t ndir_out, ndir_in;

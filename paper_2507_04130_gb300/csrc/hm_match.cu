@@ -57,8 +57,9 @@ struct Task {
   int32_t depth;   // mapped positions (>= 2)
   int32_t drive;   // driving condition index for position `depth`
   uint32_t pmask;  // candidates allowed in the first chunk [lo, lo+32)
-  int32_t pad;
-  int64_t lo, hi;  // range of the driving list (absolute offsets)
+  int32_t pid;     // pattern of the task (batched launches)
+  int32_t lo, hi;  // range of the driving list (absolute offsets)
+  int32_t pad[2];
   int32_t map[kMaxK];
 };
 static_assert(sizeof(Task) == 96, "task layout");
@@ -119,15 +120,15 @@ __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t
   if (outdeg_x == 0 || indeg_y == 0) return false;
   if (kC) ctr += 8;
   if (outdeg_x <= indeg_y) {
-    int64_t o = __ldg(&G.off[x].x);
-    int64_t i = search_c<kC>(G.out_adj, o, outdeg_x, y, ctr);
+    const int32_t o = __ldg(&G.off[x].x);
+    const int32_t i = search_c<kC>(G.out_adj, o, outdeg_x, y, ctr);
     if (i < 0) return false;
     if (kC) ctr += 4;
     *lab = __ldg(G.out_elab + i);
     return true;
   }
-  int64_t o = __ldg(&G.off[y].y);
-  int64_t i = search_c<kC>(G.in_adj, o, indeg_y, x, ctr);
+  const int32_t o = __ldg(&G.off[y].y);
+  const int32_t i = search_c<kC>(G.in_adj, o, indeg_y, x, ctr);
   if (i < 0) return false;
   if (kC) ctr += 4;
   *lab = __ldg(G.in_elab + i);
@@ -243,7 +244,7 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
 
 // Is w a neighbour (in or out) of y?
 template <bool kC>
-__device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, longlong2 oy,
+__device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, int2 oy,
                                         int32_t w, uint64_t &ctr) {
   if (iy.y && search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0) return true;
   return iy.z && search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0;
@@ -264,15 +265,15 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need, const int2 *__r
     const int2 uv = in[s];
     if (kC && lane == 0) ctr += 72;
     int4 iu = __ldg(&G.vi[uv.x]), iv = __ldg(&G.vi[uv.y]);
-    longlong2 ou = __ldg(&G.off[uv.x]), ov = __ldg(&G.off[uv.y]);
+    int2 ou = __ldg(&G.off[uv.x]), ov = __ldg(&G.off[uv.y]);
     // iterate the side with fewer incident arcs, probe the other
     const bool swap = (iu.y + iu.z) > (iv.y + iv.z);
     const int4 ix = swap ? iv : iu, iy = swap ? iu : iv;
-    const longlong2 ox = swap ? ov : ou, oy = swap ? ou : ov;
+    const int2 ox = swap ? ov : ou, oy = swap ? ou : ov;
     const int32_t y = swap ? uv.x : uv.y;
     int32_t got = 0;
     // out-neighbours of x
-    for (int64_t b = 0; b < ix.y && got < need; b += 32) {
+    for (int32_t b = 0; b < ix.y && got < need; b += 32) {
       bool hit = false;
       if (b + lane < ix.y) {
         int32_t w = __ldg(G.out_adj + ox.x + b + lane);
@@ -282,7 +283,7 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need, const int2 *__r
       got += __popc(__ballot_sync(kFull, hit));
     }
     // in-neighbours of x that are not also out-neighbours
-    for (int64_t b = 0; b < ix.z && got < need; b += 32) {
+    for (int32_t b = 0; b < ix.z && got < need; b += 32) {
       bool hit = false;
       if (b + lane < ix.z) {
         int32_t w = __ldg(G.in_adj + ox.y + b + lane);
@@ -312,12 +313,12 @@ struct WarpState {
   int32_t map[kMaxK];       // image of each mapped position
   int32_t deg_out[kMaxK];   // its out-degree
   int32_t deg_in[kMaxK];    // its in-degree
-  int64_t off_out[kMaxK];   // its first out-arc
-  int64_t off_in[kMaxK];    // its first in-arc
+  int32_t off_out[kMaxK];   // its first out-arc
+  int32_t off_in[kMaxK];    // its first in-arc
   int4 dir[kMaxK];          // its directory spans {out first, out count, in first, in count}
-  int64_t lo[kMaxK];        // next chunk of the driving group at each depth
-  int64_t hi[kMaxK];        // end of the driving range
-  int64_t base[kMaxK];      // start of the chunk whose survivors are pending
+  int32_t lo[kMaxK];        // next chunk of the driving group at each depth
+  int32_t hi[kMaxK];        // end of the driving range
+  int32_t base[kMaxK];      // start of the chunk whose survivors are pending
   uint32_t mask[kMaxK];     // pending survivors of that chunk
   int32_t drive[kMaxK];     // driving condition at each depth
   Task stage;               // task being donated or received
@@ -332,12 +333,12 @@ __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int 
   if (kC && lane == 0) ctr += 48;
   // three independent 16-byte loads spread over three lanes
   int4 vi = make_int4(0, 0, 0, 0), vd = make_int4(0, 0, 0, 0);
-  longlong2 o = make_longlong2(0, 0);
+  int2 o = make_int2(0, 0);
   if (lane == 0) vi = __ldg(&G.vi[c]);
   if (lane == 1) o = __ldg(&G.off[c]);
   if (lane == 2) vd = __ldg(&G.vdir[c]);
   const int32_t dout = __shfl_sync(kFull, vi.y, 0), din = __shfl_sync(kFull, vi.z, 0);
-  const long long oo = __shfl_sync(kFull, o.x, 1), oi = __shfl_sync(kFull, o.y, 1);
+  const int32_t oo = __shfl_sync(kFull, o.x, 1), oi = __shfl_sync(kFull, o.y, 1);
   int4 d;
   d.x = __shfl_sync(kFull, vd.x, 2);
   d.y = __shfl_sync(kFull, vd.y, 2);
@@ -397,7 +398,7 @@ __device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, Wa
   if (lane == 0 && !keep) {
     const Cons cs = P.cons[p][best];
     const int2 r = grp[P.gbase[p] + best];
-    const int64_t lo = (cs.kind == kOut ? S.off_out[cs.q] : S.off_in[cs.q]) + r.x;
+    const int32_t lo = (cs.kind == kOut ? S.off_out[cs.q] : S.off_in[cs.q]) + r.x;
     S.drive[p] = best;
     S.lo[p] = lo;
     S.hi[p] = lo + r.y;
@@ -420,7 +421,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
   // to search c's shorter list instead of a hub's
   const bool need_c = !leaf || nc > 1;
   int4 vi = make_int4(0, 0, 0, 0);
-  longlong2 oc = make_longlong2(0, 0);
+  int2 oc = make_int2(0, 0);
   if (need_c) {
 #if HM_EAGER_OFFSETS
     // both records in flight together (the offsets are used by most searches)
@@ -449,12 +450,12 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int32_t rev_len = fwd ? vi.z : vi.y;
       if (r.y == 0) return false;
       if (rev_len < r.y) {
-        const int64_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
+        const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
                               : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
         if (kC && i >= 0) ctr += 4;
         found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
       } else {
-        const int64_t base = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
+        const int32_t base = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
         found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, base, r.y, c, ctr) >= 0;
       }
       if (!found) return false;
@@ -500,13 +501,13 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
     if (r.y == 0 || rev_len == 0) return false;
     if (rev_len < r.y) {
       if (kC) ctr += 16;
-      const longlong2 oc = __ldg(&G.off[c]);
-      const int64_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
+      const int2 oc = __ldg(&G.off[c]);
+      const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
                             : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
       if (kC && i >= 0) ctr += 4;
       return i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
     }
-    const int64_t lo = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
+    const int32_t lo = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
     return search_c<kC>(fwd ? G.gout_adj : G.gin_adj, lo, r.y, c, ctr) >= 0;
   }
   const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
@@ -515,7 +516,7 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
   if (la <= lb)
     return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
   if (kC) ctr += 16;
-  const longlong2 oc = __ldg(&G.off[c]);
+  const int2 oc = __ldg(&G.off[c]);
   return search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) < 0;
 }
 
@@ -602,7 +603,7 @@ __device__ __forceinline__ bool queue_maybe_nonempty(const ExtArgs &A) {
 // depth L0 to the candidates in first_mask; a split of that window hands the
 // shifted restriction to the new task (such tasks never extend past the window).
 __device__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0, int level,
-                           int lane, int64_t first_lo, uint32_t first_mask) {
+                           int lane, int32_t first_lo, uint32_t first_mask) {
   int l = -1, kind = 0;
   for (int d = L0; d <= level; ++d) {
     if (S.hi[d] - S.lo[d] >= A.split_min) { l = d; kind = 0; break; }
@@ -613,10 +614,11 @@ __device__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0
     Task &t = S.stage;
     t.depth = l;
     t.drive = S.drive[l];
-    t.pad = 0;
+    t.pid = 0;
+    t.pad[0] = t.pad[1] = 0;
     for (int i = 0; i < kMaxK; ++i) t.map[i] = i < l ? S.map[i] : -1;
     if (kind == 0) {
-      int64_t mid = S.lo[l] + ((S.hi[l] - S.lo[l]) >> 1);
+      const int32_t mid = S.lo[l] + ((S.hi[l] - S.lo[l]) >> 1);
       t.lo = mid;
       t.hi = S.hi[l];
       t.pmask = kFull;
@@ -744,7 +746,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     }
     int L0 = 2;
     uint32_t first_mask = kFull;
-    int64_t first_lo = -1;
+    int32_t first_lo = -1;
     if (got == 2) {
       // install a donated task
       const int d = S.stage.depth;
@@ -768,8 +770,8 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     int level = L0;
     while (true) {
       if (S.mask[level] == 0) {
-        const int64_t lo = S.lo[level];
-        int64_t hi = S.hi[level];
+        const int32_t lo = S.lo[level];
+        int32_t hi = S.hi[level];
         if (lo >= hi) {
           if (level == L0) break;
           --level;
@@ -858,7 +860,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
           }
         } else {
           take = 32;
-          const int64_t idx = lo + lane;
+          const int32_t idx = lo + lane;
           if (idx < hi && ((allow >> lane) & 1u)) {
             c = __ldg(adj + idx);
             if (kC) {
