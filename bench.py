@@ -78,9 +78,11 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """Hash of the sources that define k_extend (its header and the shared device helpers)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2507_04130_gb300", "csrc", "hm_match.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("hm_kernels.cuh", "hm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2507_04130_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

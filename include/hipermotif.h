@@ -190,6 +190,29 @@ hm_status hm_enumerate_matches_part(const hm_graph *g, const hm_pattern *p, hm_m
                                     int32_t part, int32_t nparts, int32_t *rows_dev, uint64_t cap,
                                     uint64_t *count, void *stream);
 
+/* hm_count_batch / hm_enumerate_batch -- npat patterns against one graph in
+ * one pass (the HiPerMotif algorithm of Sec. III-C run for all of them at
+ * once): one scan of the target's arcs validates every arc as the seeding arc
+ * of every pattern whose signature (arc label, source label, target label) it
+ * carries, and one persistent extension launch serves the depth-2 states of
+ * all patterns.  Each result equals the pattern's own hm_count_matches /
+ * hm_enumerate_matches result.
+ *   patterns  HOST array of npat pattern handles (repeats allowed).
+ *   modes     HOST int32[npat], HM_MONO or HM_INDUCED per pattern.
+ *   counts    HOST uint64[npat] output, filled on HM_OK and on HM_ERR_CAPACITY.
+ *   rows_dev  DEVICE int32 buffer owned by the caller; pattern i's rows go to
+ *             rows_dev[row_offsets[i] .. row_offsets[i+1]) (int32 elements),
+ *             i.e. up to (row_offsets[i+1]-row_offsets[i]) / k_i rows, sorted.
+ *   row_offsets HOST uint64[npat+1], non-decreasing.
+ * If any pattern has more rows than its region holds, HM_ERR_CAPACITY with all
+ * counts set (call hm_count_batch first to size the regions).  npat == 0 is a
+ * no-op.  Errors otherwise as hm_count_matches. */
+hm_status hm_count_batch(const hm_graph *g, const hm_pattern *const *patterns,
+                         const int32_t *modes, int32_t npat, uint64_t *counts, void *stream);
+hm_status hm_enumerate_batch(const hm_graph *g, const hm_pattern *const *patterns,
+                             const int32_t *modes, int32_t npat, int32_t *rows_dev,
+                             const uint64_t *row_offsets, uint64_t *counts, void *stream);
+
 /* hm_injected_states -- the depth-2 states the edge scan produces: every
  * target arc accepted by the vertex validator (Alg. 2) and the edge
  * validator (Alg. 3) for the reordered arc between positions 0 and 1, as

@@ -26,7 +26,7 @@ from .binding import HM_MONO as MONO
 from .binding import HMError, check, lib
 
 __all__ = ["Graph", "Pattern", "count_matches", "enumerate_matches", "count_matches_rooted",
-           "count_matches_part", "enumerate_matches_part",
+           "count_matches_part", "enumerate_matches_part", "count_batch", "enumerate_batch",
            "injected_states", "set_budget", "set_timing", "set_counters", "set_tuning", "get_tuning",
            "last_stats", "MONO", "INDUCED",
            "HMError", "binding"]
@@ -208,6 +208,44 @@ def enumerate_matches_part(g: Graph, p: Pattern, mode: int, part: int, nparts: i
                                         ctypes.byref(c), _stream_ptr(stream)),
           "hm_enumerate_matches_part", int(c.value))
     return out[: int(c.value) * k].view(int(c.value), k)
+
+
+def _batch_args(patterns, modes):
+    n = len(patterns)
+    handles = (ctypes.c_void_p * max(n, 1))(*[p.handle.value for p in patterns])
+    if isinstance(modes, int):
+        modes = [modes] * n
+    m = np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
+    if m.shape[0] != n:
+        raise ValueError("one mode per pattern")
+    return n, handles, m
+
+
+def count_batch(g: Graph, patterns, modes, stream=None) -> list[int]:
+    """Counts of many patterns from one edge scan and one persistent extension launch."""
+    n, handles, m = _batch_args(patterns, modes)
+    out = np.zeros(max(n, 1), np.uint64)
+    check(lib.hm_count_batch(g.handle, ctypes.cast(handles, ctypes.c_void_p), _ptr(m), n,
+                             ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)), "hm_count_batch")
+    return [int(x) for x in out[:n]]
+
+
+def enumerate_batch(g: Graph, patterns, modes, counts=None, stream=None) -> list[torch.Tensor]:
+    """Sorted rows of many patterns in one pass; sizes the regions with a count pass if needed."""
+    n, handles, m = _batch_args(patterns, modes)
+    if counts is None:
+        counts = count_batch(g, patterns, modes, stream)
+    ks = [p.k for p in patterns]
+    offs = np.zeros(n + 1, np.uint64)
+    for i in range(n):
+        offs[i + 1] = offs[i] + np.uint64(counts[i] * ks[i])
+    buf = torch.empty(max(int(offs[-1]), 1), dtype=torch.int32, device="cuda")
+    got = np.zeros(max(n, 1), np.uint64)
+    st = lib.hm_enumerate_batch(g.handle, ctypes.cast(handles, ctypes.c_void_p), _ptr(m), n,
+                                ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(offs.ctypes.data),
+                                ctypes.c_void_p(got.ctypes.data), _stream_ptr(stream))
+    check(st, "hm_enumerate_batch")
+    return [buf[int(offs[i]): int(offs[i + 1])].view(int(got[i]), ks[i]) for i in range(n)]
 
 
 def count_matches_rooted(g: Graph, p: Pattern, mode: int, root: int, mask, stream=None) -> int:

@@ -25,7 +25,7 @@ EXPORTED = [
     "hm_enumerate_matches", "hm_count_matches_rooted", "hm_count_matches_part",
     "hm_enumerate_matches_part", "hm_injected_states", "hm_set_budget",
     "hm_last_stats", "hm_set_timing", "hm_set_counters", "hm_count_matches_static",
-    "hm_set_tuning", "hm_get_tuning",
+    "hm_set_tuning", "hm_get_tuning", "hm_count_batch", "hm_enumerate_batch",
 ]
 
 
@@ -98,6 +98,8 @@ _SIGS = {
     "hm_set_counters": (_st, [ctypes.c_int]),
     "hm_count_matches_static": (_st, [_vp, _vp, ctypes.c_int, _pu64, _vp]),
     "hm_set_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
+    "hm_count_batch": (_st, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "hm_enumerate_batch": (_st, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "hm_get_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
 }
 

@@ -1,0 +1,421 @@
+// hm_batch.cu -- many patterns against one resident graph in one pass.
+//
+// The HiPerMotif algorithm (Sec. III-C) runs one edge loop per pattern.  A
+// batch shares that loop: one scan of the target's arcs tries every arc as
+// the seeding arc of every pattern whose signature (arc label, label of the
+// arc's source, label of its target) it carries -- looked up in a small hash
+// table built on the host -- and applies that pattern's vertex and edge
+// validators (Alg. 2, Alg. 3).  Survivors carry their pattern id through the
+// overlap test and into ONE persistent extension launch, whose warps take
+// depth-2 states of any pattern and read the pattern's plan from a device
+// table.  Rows of all patterns are sorted in one stable radix sort keyed on
+// (pattern id, row), then written back to each pattern's region.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "hm_kernels.cuh"
+
+namespace hm {
+namespace {
+
+// seeding-arc signature table (open addressing, linear probing)
+struct SigKey {
+  int32_t lab, vsrc, vdst, used;
+};
+
+__device__ __host__ __forceinline__ uint32_t sig_hash(int32_t lab, int32_t vs, int32_t vd) {
+  uint32_t h = (uint32_t)lab * 0x9E3779B1u;
+  h ^= (uint32_t)vs + 0x7F4A7C15u + (h << 6) + (h >> 2);
+  h ^= (uint32_t)vd + 0x94D049BBu + (h << 6) + (h >> 2);
+  return h;
+}
+
+struct SigTable {
+  const SigKey *keys;
+  const int2 *vals;       // {first, count} into pids
+  const int32_t *pids;    // patterns sharing a signature
+  uint32_t mask;
+};
+
+// The batch's seed test for one (arc, pattern) pair: Alg. 2 on the position-0
+// image and Alg. 3's label, opposite-arc and degree checks, with the seeding
+// direction of that pattern.
+__device__ __forceinline__ bool seed_test_batch(const DevGraph &G, const Plan &P, int32_t a,
+                                                int32_t b, int4 ia, int4 ib, int2 *out) {
+  const int32_t u = P.seed_rev ? b : a;
+  const int32_t v = P.seed_rev ? a : b;
+  const int4 iu = P.seed_rev ? ib : ia;
+  const int4 iv = P.seed_rev ? ia : ib;
+  if (iu.y < P.dout[0] || iu.z < P.din[0]) return false;
+  if (iv.y < P.dout[1] || iv.z < P.din[1]) return false;
+  if (P.back_req | P.back_forbid) {
+    int32_t lab = 0;
+    uint64_t unused = 0;
+    const bool found = arc_lookup<false>(G, b, a, ib.y, ia.z, &lab, unused);
+    if (P.back_req && (!found || lab != P.back_lab)) return false;
+    if (P.back_forbid && found) return false;
+  }
+  *out = make_int2(u, v);
+  return true;
+}
+
+// Pass 1 (kWrite = false) counts the (arc, pattern) survivors; pass 2 writes
+// them.  One atomic per warp and round reserves the warp's output slots.
+template <bool kWrite>
+__global__ void __launch_bounds__(kSeedThreads)
+k_edge_seed_batch(const __grid_constant__ DevGraph G, const Plan *__restrict__ plans,
+                  const __grid_constant__ SigTable T, int2 *__restrict__ seeds,
+                  int32_t *__restrict__ seed_pid, unsigned long long cap,
+                  unsigned long long *__restrict__ nseeds) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e0 = (int64_t)blockIdx.x * kSeedThreads; e0 < G.m;
+       e0 += (int64_t)gridDim.x * kSeedThreads) {
+    const int64_t e = e0 + threadIdx.x;
+    int32_t first = 0, cnt = 0, a = 0, b = 0;
+    int4 ia = make_int4(0, 0, 0, 0), ib = ia;
+    if (e < G.m) {
+      a = __ldg(G.src + e);
+      b = __ldg(G.out_adj + e);
+      const int32_t l = __ldg(G.out_elab + e);
+      ia = __ldg(&G.vi[a]);
+      ib = __ldg(&G.vi[b]);
+      uint32_t h = sig_hash(l, ia.x, ib.x) & T.mask;
+      for (uint32_t probe = 0; probe <= T.mask; ++probe, h = (h + 1) & T.mask) {
+        const SigKey k = T.keys[h];
+        if (!k.used) break;
+        if (k.lab == l && k.vsrc == ia.x && k.vdst == ib.x) {
+          const int2 r = T.vals[h];
+          first = r.x;
+          cnt = r.y;
+          break;
+        }
+      }
+    }
+    // count this arc's survivors, then reserve slots warp-wide
+    uint32_t mine = 0;
+    for (int32_t i = 0; i < cnt; ++i) {
+      int2 uv;
+      mine += seed_test_batch(G, plans[T.pids[first + i]], a, b, ia, ib, &uv);
+    }
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(nseeds, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    if (kWrite && mine) {
+      unsigned long long at = base + incl - mine;
+      for (int32_t i = 0; i < cnt; ++i) {
+        const int32_t pid = T.pids[first + i];
+        int2 uv;
+        if (seed_test_batch(G, plans[pid], a, b, ia, ib, &uv)) {
+          if (at < cap) {
+            seeds[at] = uv;
+            seed_pid[at] = pid;
+          }
+          ++at;
+        }
+      }
+    }
+  }
+}
+
+// Rows of every pattern, padded to width kmax+1 with the pattern id first.
+__global__ void k_pack_rows(const int32_t *__restrict__ rows, const unsigned long long *__restrict__ off,
+                            const unsigned long long *__restrict__ start, const int32_t *__restrict__ ks,
+                            int32_t npat, unsigned long long total, int width,
+                            int32_t *__restrict__ packed) {
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = npat - 1;  // last pattern whose start <= t
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int32_t p = lo, k = ks[p];
+    const int32_t *src = rows + off[p] + (t - start[p]) * k;
+    int32_t *dst = packed + t * width;
+    dst[0] = p;
+    for (int c = 0; c < width - 1; ++c) dst[1 + c] = c < k ? src[c] : 0;
+  }
+}
+
+__global__ void k_unpack_rows(const int32_t *__restrict__ packed, const unsigned long long *__restrict__ off,
+                              const unsigned long long *__restrict__ start, const int32_t *__restrict__ ks,
+                              unsigned long long total, int width, int32_t *__restrict__ rows) {
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    const int32_t *src = packed + t * width;
+    const int32_t p = src[0], k = ks[p];
+    int32_t *dst = rows + off[p] + (t - start[p]) * k;
+    for (int c = 0; c < k; ++c) dst[c] = src[1 + c];
+  }
+}
+
+hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int32_t *modes,
+                    int32_t npat, int32_t *rows, const uint64_t *row_offsets, uint64_t *counts,
+                    cudaStream_t s) {
+  if (!g || npat < 0 || (npat > 0 && (!pats || !modes || !counts))) return HM_ERR_ARG;
+  if (npat == 0) return HM_OK;
+  const bool want_rows = rows != nullptr || row_offsets != nullptr;
+  if (want_rows && (!rows || !row_offsets)) return HM_ERR_ARG;
+  ensure_pool();
+  hm_stats &st = tls_stats();
+  std::memset(&st, 0, sizeof(st));
+  const bool timing = timing_enabled();
+
+  // ---- host tables: plans, signatures, row regions
+  std::vector<Plan> plans(npat);
+  std::vector<int32_t> ks(npat);
+  int32_t grp_slots = 0, kmax = 0;
+  for (int32_t i = 0; i < npat; ++i) {
+    if (!pats[i] || (modes[i] != HM_MONO && modes[i] != HM_INDUCED)) return HM_ERR_ARG;
+    plans[i] = pats[i]->plan[modes[i]];
+    ks[i] = pats[i]->k;
+    grp_slots = std::max(grp_slots, plans[i].ngrp);
+    kmax = std::max(kmax, ks[i]);
+  }
+  std::vector<unsigned long long> off(npat + 1, 0), cap(npat, 0);
+  if (want_rows) {
+    for (int32_t i = 0; i < npat; ++i) {
+      if (row_offsets[i + 1] < row_offsets[i]) return HM_ERR_ARG;
+      off[i] = row_offsets[i];
+      cap[i] = (row_offsets[i + 1] - row_offsets[i]) / (uint64_t)ks[i];
+    }
+  }
+  // signature (arc label, label of the arc's source, label of its target) -> patterns
+  struct Sig {
+    int32_t lab, vs, vd, pid;
+  };
+  std::vector<Sig> sigs(npat);
+  for (int32_t i = 0; i < npat; ++i) {
+    const Plan &P = plans[i];
+    // normal seeding: arc (f(0), f(1)); reversed: arc (f(1), f(0))
+    sigs[i] = P.seed_rev ? Sig{P.seed_lab, P.vlab[1], P.vlab[0], i} : Sig{P.seed_lab, P.vlab[0], P.vlab[1], i};
+  }
+  std::sort(sigs.begin(), sigs.end(), [](const Sig &x, const Sig &y) {
+    if (x.lab != y.lab) return x.lab < y.lab;
+    if (x.vs != y.vs) return x.vs < y.vs;
+    if (x.vd != y.vd) return x.vd < y.vd;
+    return x.pid < y.pid;
+  });
+  uint32_t tsize = 16;
+  while (tsize < 2u * (uint32_t)npat) tsize <<= 1;
+  std::vector<SigKey> keys(tsize, SigKey{0, 0, 0, 0});
+  std::vector<int2> vals(tsize, make_int2(0, 0));
+  std::vector<int32_t> pid_list(npat);
+  for (int32_t i = 0; i < npat;) {
+    int32_t j = i;
+    while (j < npat && sigs[j].lab == sigs[i].lab && sigs[j].vs == sigs[i].vs && sigs[j].vd == sigs[i].vd) {
+      pid_list[j] = sigs[j].pid;
+      ++j;
+    }
+    uint32_t h = sig_hash(sigs[i].lab, sigs[i].vs, sigs[i].vd) & (tsize - 1);
+    while (keys[h].used) h = (h + 1) & (tsize - 1);
+    keys[h] = SigKey{sigs[i].lab, sigs[i].vs, sigs[i].vd, 1};
+    vals[h] = make_int2(i, j - i);
+    i = j;
+  }
+
+  // ---- device copies
+  Scratch sc(s);
+  Plan *d_plans;
+  SigKey *d_keys;
+  int2 *d_vals;
+  int32_t *d_pids, *d_ks;
+  unsigned long long *d_ull;  // counts, off, cap, cursor, start, nseeds x2
+  Ctl *ctl;
+  HM_CUDA_TRY(sc.get((void **)&d_plans, sizeof(Plan) * npat));
+  HM_CUDA_TRY(sc.get((void **)&d_keys, sizeof(SigKey) * tsize));
+  HM_CUDA_TRY(sc.get((void **)&d_vals, sizeof(int2) * tsize));
+  HM_CUDA_TRY(sc.get((void **)&d_pids, sizeof(int32_t) * npat));
+  HM_CUDA_TRY(sc.get((void **)&d_ks, sizeof(int32_t) * npat));
+  HM_CUDA_TRY(sc.get((void **)&d_ull, sizeof(unsigned long long) * (size_t)(5 * npat + 2)));
+  HM_CUDA_TRY(sc.get((void **)&ctl, sizeof(Ctl)));
+  unsigned long long *d_counts = d_ull, *d_off = d_ull + npat, *d_cap = d_ull + 2 * npat,
+                     *d_cursor = d_ull + 3 * npat, *d_start = d_ull + 4 * npat;
+  HM_CUDA_TRY(cudaMemcpyAsync(d_plans, plans.data(), sizeof(Plan) * npat, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemcpyAsync(d_keys, keys.data(), sizeof(SigKey) * tsize, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemcpyAsync(d_vals, vals.data(), sizeof(int2) * tsize, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemcpyAsync(d_pids, pid_list.data(), sizeof(int32_t) * npat, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemcpyAsync(d_ks, ks.data(), sizeof(int32_t) * npat, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemsetAsync(d_ull, 0, sizeof(unsigned long long) * (size_t)(5 * npat + 2), s));
+  HM_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), sizeof(unsigned long long) * npat, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemcpyAsync(d_cap, cap.data(), sizeof(unsigned long long) * npat, cudaMemcpyHostToDevice, s));
+  HM_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  const SigTable T{d_keys, d_vals, d_pids, tsize - 1};
+  const DevGraph G = g->dev();
+  const int64_t m = g->m;
+  const int sms = num_sms();
+  uint32_t launches = 0;
+
+  // ---- edge scan: count, size, write
+  Timer t_edge(s, timing);
+  const int grid_e = (int)std::max<int64_t>(1, std::min<int64_t>((m + kSeedThreads - 1) / kSeedThreads,
+                                                                   (int64_t)sms * 8));
+  unsigned long long nraw = 0;
+  if (m) {
+    k_edge_seed_batch<false><<<grid_e, kSeedThreads, 0, s>>>(G, d_plans, T, nullptr, nullptr, 0,
+                                                             &ctl->nseeds_raw);
+    HM_CUDA_TRY(cudaMemcpyAsync(&nraw, &ctl->nseeds_raw, sizeof(nraw), cudaMemcpyDeviceToHost, s));
+    HM_CUDA_TRY(cudaStreamSynchronize(s));
+    launches += 1;
+  }
+  int2 *seeds_a, *seeds_b;
+  int32_t *pid_a, *pid_b;
+  HM_CUDA_TRY(sc.get((void **)&seeds_a, sizeof(int2) * (size_t)std::max<unsigned long long>(nraw, 1)));
+  HM_CUDA_TRY(sc.get((void **)&pid_a, sizeof(int32_t) * (size_t)std::max<unsigned long long>(nraw, 1)));
+  HM_CUDA_TRY(sc.get((void **)&seeds_b, sizeof(int2) * (size_t)std::max<unsigned long long>(nraw, 1)));
+  HM_CUDA_TRY(sc.get((void **)&pid_b, sizeof(int32_t) * (size_t)std::max<unsigned long long>(nraw, 1)));
+  if (nraw) {
+    HM_CUDA_TRY(cudaMemsetAsync(&ctl->nseeds_raw, 0, sizeof(unsigned long long), s));
+    k_edge_seed_batch<true><<<grid_e, kSeedThreads, 0, s>>>(G, d_plans, T, seeds_a, pid_a, nraw,
+                                                            &ctl->nseeds_raw);
+    launches += 1;
+  }
+  t_edge.stop();
+  HM_CUDA_TRY(cudaGetLastError());
+  // ---- overlap test (patterns without one pass their seeds through)
+  bool any_ov = false;
+  for (const Plan &P : plans) any_ov |= P.ov_need > 0;
+  const int2 *seeds = seeds_a;
+  const int32_t *seed_pid = pid_a;
+  const unsigned long long *nseeds = &ctl->nseeds_raw;
+  Timer t_ov(s, timing && any_ov);
+  if (any_ov && nraw) {
+    k_seed_overlap<false, true><<<sms * 8, kSeedThreads, 0, s>>>(G, 0, seeds_a, &ctl->nseeds_raw, seeds_b,
+                                                                  nraw, &ctl->nseeds, &ctl->bytes_overlap,
+                                                                  d_plans, pid_a, pid_b);
+    launches += 1;
+    seeds = seeds_b;
+    seed_pid = pid_b;
+    nseeds = &ctl->nseeds;
+  }
+  t_ov.stop();
+
+  // ---- one persistent extension launch for every pattern
+  Task *qbuf;
+  unsigned long long *qseq;
+  HM_CUDA_TRY(sc.get((void **)&qbuf, sizeof(Task) * kQueueCap));
+  HM_CUDA_TRY(sc.get((void **)&qseq, sizeof(unsigned long long) * kQueueCap));
+  k_qinit<<<64, 256, 0, s>>>(qseq);
+  launches += 1;
+  ExtArgs A{};
+  const hm_tuning tu = tuning();
+  A.split_min = tu.split_min;
+  A.pair_mode = tu.pair_mode;
+  A.seeds_per_fetch = tu.seeds_per_fetch;
+  A.poll_mask = (uint32_t)tu.poll_every - 1u;
+  A.seeds = seeds;
+  A.nseeds = nseeds;
+  A.qbuf = qbuf;
+  A.qseq = qseq;
+  A.ctl = ctl;
+  A.rows = rows;
+  A.cap = 0;
+  A.root_mask = nullptr;
+  A.budget_ns = budget_ms() * 1000000ull;
+  A.max_chunks = budget_chunks();
+  A.plans = d_plans;
+  A.seed_pid = seed_pid;
+  A.counts = d_counts;
+  A.row_off = d_off;
+  A.row_cap = d_cap;
+  A.row_cursor = d_cursor;
+  A.grp_slots = grp_slots;
+  const int slot = min_blocks_slot(tu.extend_min_blocks);
+  const size_t smem = warp_smem_bytes(grp_slots) * kExtWarps;
+  const bool counters = counters_enabled();
+  const int grid = extend_grid<true>(want_rows, counters, smem, slot);
+  if (grid <= 0) return HM_ERR_CUDA;
+  st.extend_grid = grid;
+  st.extend_block = kExtThreads;
+  Timer t_ext(s, timing);
+  extend_kernel<true>(want_rows, counters, slot)<<<grid, kExtThreads, smem, s>>>(G, plans[0], A);
+  launches += 1;
+  t_ext.stop();
+  HM_CUDA_TRY(cudaGetLastError());
+  Ctl h;
+  std::vector<unsigned long long> hc(npat);
+  HM_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  HM_CUDA_TRY(cudaMemcpyAsync(hc.data(), d_counts, sizeof(unsigned long long) * npat,
+                              cudaMemcpyDeviceToHost, s));
+  HM_CUDA_TRY(cudaStreamSynchronize(s));
+  st.ms_edge_scan = t_edge.ms();
+  st.ms_overlap = t_ov.ms();
+  st.ms_extend = t_ext.ms();
+  st.seeds_scanned = (uint64_t)m;
+  st.states_injected = any_ov ? h.nseeds : h.nseeds_raw;
+  st.tasks_donated = h.donated;
+  st.chunks = h.chunks;
+  st.bytes_extend = h.bytes_extend;
+  st.candidates = h.lanes;
+  if (h.status == kStatBudget) return HM_ERR_BUDGET;
+  if (h.status != kStatOk) return HM_ERR_CUDA;
+  uint64_t total = 0;
+  bool over = false;
+  for (int32_t i = 0; i < npat; ++i) {
+    counts[i] = hc[i];
+    total += hc[i];
+    if (want_rows && hc[i] > cap[i]) over = true;
+  }
+  st.matches = total;
+  st.kernel_launches = launches;
+  if (!want_rows) return HM_OK;
+  if (over) return HM_ERR_CAPACITY;
+  if (total == 0) return HM_OK;
+
+  // ---- one sort for all patterns: key (pattern id, row), then back to each region
+  Timer t_sort(s, timing);
+  std::vector<unsigned long long> start(npat + 1, 0);
+  for (int32_t i = 0; i < npat; ++i) start[i + 1] = start[i] + hc[i];
+  HM_CUDA_TRY(cudaMemcpyAsync(d_start, start.data(), sizeof(unsigned long long) * npat,
+                              cudaMemcpyHostToDevice, s));
+  const int width = kmax + 1;
+  int32_t *packed, *tmp;
+  HM_CUDA_TRY(sc.get((void **)&packed, sizeof(int32_t) * (size_t)total * width));
+  HM_CUDA_TRY(sc.get((void **)&tmp, sizeof(int32_t) * (size_t)total * width));
+  const int grid_r = (int)std::max<uint64_t>(1, std::min<uint64_t>((total + 255) / 256, (uint64_t)sms * 16));
+  k_pack_rows<<<grid_r, 256, 0, s>>>(rows, d_off, d_start, d_ks, npat, total, width, packed);
+  int cols[kMaxK + 1], bits[kMaxK + 1];
+  uint32_t xr[kMaxK + 1];
+  for (int c = 0; c < width; ++c) {
+    cols[c] = c;
+    bits[c] = c == 0 ? bits_for(npat) : bits_for(g->n);
+    xr[c] = 0;
+  }
+  hm_status r = radix_sort_rows_cols(packed, tmp, (int64_t)total, width, cols, bits, xr, width, s);
+  if (r != HM_OK) return r;
+  k_unpack_rows<<<grid_r, 256, 0, s>>>(packed, d_off, d_start, d_ks, total, width, rows);
+  t_sort.stop();
+  HM_CUDA_TRY(cudaGetLastError());
+  int total_bits = bits_for(npat) + kmax * bits_for(g->n);
+  st.kernel_launches += 2 + 5 * ((total_bits + 7) / 8);
+  if (timing) {
+    HM_CUDA_TRY(cudaStreamSynchronize(s));
+    st.ms_sort = t_sort.ms();
+  }
+  return HM_OK;
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_count_batch(const hm_graph *g, const hm_pattern *const *patterns,
+                                    const int32_t *modes, int32_t npat, uint64_t *counts,
+                                    void *stream) {
+  return hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, counts, (cudaStream_t)stream);
+}
+
+extern "C" hm_status hm_enumerate_batch(const hm_graph *g, const hm_pattern *const *patterns,
+                                        const int32_t *modes, int32_t npat, int32_t *rows_dev,
+                                        const uint64_t *row_offsets, uint64_t *counts,
+                                        void *stream) {
+  if (npat > 0 && (!rows_dev || !row_offsets)) return HM_ERR_ARG;
+  return hm::run_batch(g, patterns, modes, npat, rows_dev, row_offsets, counts, (cudaStream_t)stream);
+}

@@ -19,6 +19,7 @@
 // and Alg. 3 applied as a range lookup instead of per candidate).
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "hm_internal.cuh"
 
@@ -183,16 +184,15 @@ void label_key(int32_t lo, int32_t hi, int *bits, uint32_t *xr) {
 
 struct Temps {
   cudaStream_t s;
-  void *p[12] = {};
-  int n = 0;
-  explicit Temps(cudaStream_t st) : s(st) {}
+  std::vector<void *> p;
+  explicit Temps(cudaStream_t st) : s(st) { p.reserve(16); }
   cudaError_t get(void **out, size_t bytes) {
     cudaError_t e = cudaMallocAsync(out, bytes ? bytes : 16, s);
-    if (e == cudaSuccess) p[n++] = *out;
+    if (e == cudaSuccess) p.push_back(*out);
     return e;
   }
   ~Temps() {
-    for (int i = 0; i < n; ++i) cudaFreeAsync(p[i], s);
+    for (void *q : p) cudaFreeAsync(q, s);
   }
 };
 

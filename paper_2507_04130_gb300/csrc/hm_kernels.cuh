@@ -1,0 +1,1107 @@
+// hm_kernels.cuh -- device code of the matching path, shared by the single-pattern
+// (hm_match.cu) and batched (hm_batch.cu) entry points.  Each translation unit
+// that includes it gets its own copy of these kernels.
+//
+//
+//   k_edge_seed     every target arc is tried as the image of the reordered
+//                   pattern arc between positions 0 and 1 (the loop "for all
+//                   e in E2" of the HiPerMotif algorithm): vertex validator
+//                   (Alg. 2) on the position-0 image, edge validator (Alg. 3)
+//                   label, opposite-arc and degree checks.  Arcs stream in
+//                   CSR order with int4 loads; survivors are compacted with
+//                   warp ballots and a block scan into the seed queue.
+//   k_seed_overlap  the edge validator's neighbour-overlap test
+//                   |N_u & N_v| >= |N_0 & N_1|, one warp per surviving arc,
+//                   launched only when the right side is non-zero.
+//   k_extend        state injection and extension: each seed is a depth-2
+//                   partial mapping; a persistent kernel extends it vertex by
+//                   vertex, one warp per state.  At each depth the candidates
+//                   are the shortest anchor list (the out- or in-list of an
+//                   already-mapped neighbour), scanned 32 at a time; each lane
+//                   checks one candidate (injectivity, label, degrees, the
+//                   other arcs by binary search, induced non-arcs) and a
+//                   ballot gives the survivors.  The depth-first stack lives in
+//                   shared memory.  Idle warps advertise themselves; busy warps
+//                   split the shallowest unfinished range and donate half
+//                   through a bounded lock-free queue.  Every wait is bounded
+//                   by the call's time budget.
+//   k_seed_rows     two-vertex patterns: each seed is already a match.
+//
+// Output: a match count (uint64), and optionally rows in original pattern
+// order written at an atomic cursor and then radix-sorted lexicographically
+// (hm_sort.cu), which makes the final order deterministic.
+#pragma once
+
+#include <cuda/atomic>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hm_internal.cuh"
+
+// 1: load a candidate's offsets together with its label/degree record;
+// 0: only after it passes the degree filter.
+#ifndef HM_EAGER_OFFSETS
+#define HM_EAGER_OFFSETS 0
+#endif
+
+namespace hm {
+
+void ensure_pool();
+
+namespace {
+
+constexpr int kExtThreads = 256;
+constexpr int kExtWarps = kExtThreads / 32;
+constexpr int kSeedThreads = 256;
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint64_t kQueueCap = 1ull << 16;  // donated tasks in flight (power of two)
+
+struct Task {
+  int32_t depth;   // mapped positions (>= 2)
+  int32_t drive;   // driving condition index for position `depth`
+  uint32_t pmask;  // candidates allowed in the first chunk [lo, lo+32)
+  int32_t pid;     // pattern of the task (batched launches)
+  int32_t lo, hi;  // range of the driving list (absolute offsets)
+  int32_t pad[2];
+  int32_t map[kMaxK];
+};
+static_assert(sizeof(Task) == 96, "task layout");
+constexpr int kTaskWords = sizeof(Task) / 4;
+
+// Control block of one call.  Words that different warps hit at high rates
+// sit on separate 128-byte lines so they do not contend for one cache line.
+struct Ctl {
+  alignas(128) unsigned long long seed_next;  // next unclaimed seed
+  alignas(128) unsigned long long head;       // donation queue
+  unsigned long long tail;
+  alignas(128) int32_t active;                // warps that hold work
+  alignas(128) int32_t hungry;                // warps waiting for work
+  int32_t requests;                           // donations asked for, not yet claimed
+  alignas(128) int32_t status;
+  alignas(128) unsigned long long nseeds_raw; // arcs passing the edge scan
+  unsigned long long nseeds;                  // after the overlap test
+  unsigned long long count;
+  unsigned long long rows_written;
+  unsigned long long chunks;
+  unsigned long long donated;
+  unsigned long long bytes_edge;              // algorithmic bytes (instrumented launches only)
+  unsigned long long bytes_overlap;
+  unsigned long long bytes_extend;
+  unsigned long long lanes;                   // candidates examined (instrumented launches only)
+};
+
+struct ExtArgs {
+  int32_t split_min;        // donate a range only while it holds at least this many candidates
+  int32_t pair_mode;        // spread (candidate, condition) pairs over lanes on short ranges
+  int32_t seeds_per_fetch;  // seeds a warp claims at once
+  uint32_t poll_mask;       // a busy warp looks for donation requests every poll_mask+1 chunks
+  const int2 *seeds;
+  const unsigned long long *nseeds;
+  Task *qbuf;
+  unsigned long long *qseq;
+  Ctl *ctl;
+  int32_t *rows;
+  unsigned long long cap;
+  const uint8_t *root_mask;
+  unsigned long long budget_ns;
+  unsigned long long max_chunks;
+  // batched launches (k_extend<..., kBatch = true>): one plan per pattern, the
+  // pattern of each seed, and per-pattern counts and row regions
+  const Plan *plans;
+  const int32_t *seed_pid;
+  unsigned long long *counts;
+  const unsigned long long *row_off;  // first int32 of each pattern's rows in `rows`
+  const unsigned long long *row_cap;  // rows each pattern may write
+  unsigned long long *row_cursor;     // rows each pattern has claimed
+  int32_t grp_slots;                  // group slots per warp (max over the patterns)
+  int32_t pad2;
+};
+
+using atomic_u64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
+using atomic_i32 = cuda::atomic_ref<int32_t, cuda::thread_scope_device>;
+
+__device__ __forceinline__ int32_t ld_volatile(const int32_t *p) {
+  return *(const volatile int32_t *)p;
+}
+
+// ---------------------------------------------------------------------------
+// arc lookup: is (x -> y) an arc?  Searches the shorter of out(x) and in(y).
+// ---------------------------------------------------------------------------
+template <bool kC>
+__device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t y, int32_t outdeg_x,
+                                           int32_t indeg_y, int32_t *lab, uint64_t &ctr) {
+  if (outdeg_x == 0 || indeg_y == 0) return false;
+  if (kC) ctr += 8;
+  if (outdeg_x <= indeg_y) {
+    const int32_t o = __ldg(&G.off[x].x);
+    const int32_t i = search_c<kC>(G.out_adj, o, outdeg_x, y, ctr);
+    if (i < 0) return false;
+    if (kC) ctr += 4;
+    *lab = __ldg(G.out_elab + i);
+    return true;
+  }
+  const int32_t o = __ldg(&G.off[y].y);
+  const int32_t i = search_c<kC>(G.in_adj, o, indeg_y, x, ctr);
+  if (i < 0) return false;
+  if (kC) ctr += 4;
+  *lab = __ldg(G.in_elab + i);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// edge scan: vertex validator + edge validator (label, opposite arc, degrees)
+// ---------------------------------------------------------------------------
+template <bool kC>
+__device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int32_t a, int32_t b,
+                                          int32_t l, const uint8_t *root_mask, int2 *out,
+                                          uint64_t &ctr) {
+  if (l != P.seed_lab) return false;                       // match(e1, e2)
+  const int32_t u = P.seed_rev ? b : a;                     // image of position 0
+  const int32_t v = P.seed_rev ? a : b;                     // image of position 1
+  if (kC) ctr += 16;
+  const int4 iu = __ldg(&G.vi[u]);                          // Alg. 2 on u
+  if (iu.x != P.vlab[0] || iu.y < P.dout[0] || iu.z < P.din[0]) return false;
+  if (kC) ctr += 16;
+  const int4 iv = __ldg(&G.vi[v]);                          // match(v, 1) + degrees
+  if (iv.x != P.vlab[1] || iv.y < P.dout[1] || iv.z < P.din[1]) return false;
+  if (root_mask && ((P.root_pos == 0 && !root_mask[u]) || (P.root_pos == 1 && !root_mask[v])))
+    return false;
+  if (P.back_req | P.back_forbid) {
+    // the arc opposite to the seeding one is (b -> a) in both seeding directions
+    const int4 ib = P.seed_rev ? iu : iv;
+    const int4 ia = P.seed_rev ? iv : iu;
+    int32_t lab = 0;
+    bool found = arc_lookup<kC>(G, b, a, ib.y, ia.z, &lab, ctr);
+    if (P.back_req && (!found || lab != P.back_lab)) return false;
+    if (P.back_forbid && found) return false;
+  }
+  *out = make_int2(u, v);
+  if (kC) ctr += 8;
+  return true;
+}
+
+template <bool kC>
+__global__ void __launch_bounds__(kSeedThreads)
+k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
+            const uint8_t *__restrict__ root_mask, int2 *__restrict__ seeds,
+            unsigned long long cap, unsigned long long *__restrict__ nseeds,
+            unsigned long long *__restrict__ bytes, int64_t e_begin, int64_t e_end) {
+  uint64_t ctr = 0;
+  __shared__ uint32_t s_warp[kSeedThreads / 32];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // arcs [e_begin, e_end), e_begin a multiple of 4 so the int4 streams stay aligned
+  const int64_t ngroups = (e_end - e_begin + 3) >> 2;
+  const int64_t full_groups = (e_end - e_begin) >> 2;
+  const int4 *src4 = reinterpret_cast<const int4 *>(G.src + e_begin);
+  const int4 *dst4 = reinterpret_cast<const int4 *>(G.out_adj + e_begin);
+  const int4 *lab4 = reinterpret_cast<const int4 *>(G.out_elab + e_begin);
+  for (int64_t g0 = (int64_t)blockIdx.x * kSeedThreads; g0 < ngroups;
+       g0 += (int64_t)gridDim.x * kSeedThreads) {
+    const int64_t gi = g0 + threadIdx.x;
+    int2 s[4];
+    bool ok[4] = {false, false, false, false};
+    if (gi < full_groups) {
+      int4 a = __ldcs(src4 + gi), b = __ldcs(dst4 + gi), l = __ldcs(lab4 + gi);
+      if (kC) ctr += 48;
+      ok[0] = seed_test<kC>(G, P, a.x, b.x, l.x, root_mask, &s[0], ctr);
+      ok[1] = seed_test<kC>(G, P, a.y, b.y, l.y, root_mask, &s[1], ctr);
+      ok[2] = seed_test<kC>(G, P, a.z, b.z, l.z, root_mask, &s[2], ctr);
+      ok[3] = seed_test<kC>(G, P, a.w, b.w, l.w, root_mask, &s[3], ctr);
+    } else if (gi < ngroups) {
+      for (int j = 0; j < 4; ++j) {
+        int64_t e = e_begin + gi * 4 + j;
+        if (kC && e < e_end) ctr += 12;
+        if (e < e_end)
+          ok[j] = seed_test<kC>(G, P, G.src[e], G.out_adj[e], G.out_elab[e], root_mask, &s[j], ctr);
+      }
+    }
+    uint32_t cnt = (uint32_t)ok[0] + ok[1] + ok[2] + ok[3];
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      for (int w = 0; w < kSeedThreads / 32; ++w) {
+        uint32_t t = s_warp[w];
+        s_warp[w] = acc;
+        acc += t;
+      }
+      s_base = acc ? atomicAdd(nseeds, (unsigned long long)acc) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long at = s_base + s_warp[warp] + (incl - cnt);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (ok[j]) {
+        if (at < cap) seeds[at] = s[j];
+        ++at;
+      }
+    }
+    __syncthreads();
+  }
+  if (kC) {
+    for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
+    if (lane == 0 && ctr) atomicAdd(bytes, (unsigned long long)ctr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// neighbour-overlap test, one warp per seed
+// ---------------------------------------------------------------------------
+
+// Is w a neighbour (in or out) of y?
+template <bool kC>
+__device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, int2 oy,
+                                        int32_t w, uint64_t &ctr) {
+  if (iy.y && search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0) return true;
+  return iy.z && search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0;
+}
+
+// In batched launches (kB) each seed carries its pattern id; the threshold is
+// that pattern's, and seeds of patterns without an overlap test pass through.
+template <bool kC, bool kB = false>
+__global__ void __launch_bounds__(kSeedThreads)
+k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 *__restrict__ in,
+               const unsigned long long *__restrict__ nin, int2 *__restrict__ out,
+               unsigned long long cap, unsigned long long *__restrict__ nout,
+               unsigned long long *__restrict__ bytes, const Plan *__restrict__ plans = nullptr,
+               const int32_t *__restrict__ pid_in = nullptr, int32_t *__restrict__ pid_out = nullptr) {
+  uint64_t ctr = 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_in = (int64_t)*nin;
+  for (int64_t s = wid; s < n_in; s += nw) {
+    const int2 uv = in[s];
+    const int32_t pid = kB ? pid_in[s] : 0;
+    const int32_t need = kB ? plans[pid].ov_need : need_all;
+    if (kC && lane == 0) ctr += 72;
+    int4 iu = __ldg(&G.vi[uv.x]), iv = __ldg(&G.vi[uv.y]);
+    int2 ou = __ldg(&G.off[uv.x]), ov = __ldg(&G.off[uv.y]);
+    // iterate the side with fewer incident arcs, probe the other
+    const bool swap = (iu.y + iu.z) > (iv.y + iv.z);
+    const int4 ix = swap ? iv : iu, iy = swap ? iu : iv;
+    const int2 ox = swap ? ov : ou, oy = swap ? ou : ov;
+    const int32_t y = swap ? uv.x : uv.y;
+    int32_t got = 0;
+    // out-neighbours of x
+    for (int32_t b = 0; b < ix.y && got < need; b += 32) {
+      bool hit = false;
+      if (b + lane < ix.y) {
+        int32_t w = __ldg(G.out_adj + ox.x + b + lane);
+        if (kC) ctr += 4;
+        hit = in_nbhd<kC>(G, y, iy, oy, w, ctr);
+      }
+      got += __popc(__ballot_sync(kFull, hit));
+    }
+    // in-neighbours of x that are not also out-neighbours
+    for (int32_t b = 0; b < ix.z && got < need; b += 32) {
+      bool hit = false;
+      if (b + lane < ix.z) {
+        int32_t w = __ldg(G.in_adj + ox.y + b + lane);
+        if (kC) ctr += 4;
+        bool dup = ix.y && search_c<kC>(G.out_adj, ox.x, ix.y, w, ctr) >= 0;
+        hit = !dup && in_nbhd<kC>(G, y, iy, oy, w, ctr);
+      }
+      got += __popc(__ballot_sync(kFull, hit));
+    }
+    if (got >= need && lane == 0) {
+      unsigned long long at = atomicAdd(nout, 1ull);
+      if (at < cap) {
+        out[at] = uv;
+        if (kB) pid_out[at] = pid;
+      }
+      if (kC) ctr += 8;
+    }
+  }
+  if (kC) {
+    for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
+    if (lane == 0 && ctr) atomicAdd(bytes, (unsigned long long)ctr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent extension kernel
+// ---------------------------------------------------------------------------
+
+struct WarpState {
+  int32_t map[kMaxK];       // image of each mapped position
+  int32_t deg_out[kMaxK];   // its out-degree
+  int32_t deg_in[kMaxK];    // its in-degree
+  int32_t off_out[kMaxK];   // its first out-arc
+  int32_t off_in[kMaxK];    // its first in-arc
+  int4 dir[kMaxK];          // its directory spans {out first, out count, in first, in count}
+  int32_t lo[kMaxK];        // next chunk of the driving group at each depth
+  int32_t hi[kMaxK];        // end of the driving range
+  int32_t base[kMaxK];      // start of the chunk whose survivors are pending
+  uint32_t mask[kMaxK];     // pending survivors of that chunk
+  int32_t drive[kMaxK];     // driving condition at each depth
+  Task stage;               // task being donated or received
+};
+// Each warp's WarpState is followed in shared memory by one int2 per positive
+// condition of the pattern, {first, length} of the matching label group inside
+// the anchor's list (first relative to the list start); Plan::gbase[p] indexes it.
+
+template <bool kC>
+__device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int pos, int32_t c,
+                                           int lane, uint64_t &ctr) {
+  if (kC && lane == 0) ctr += 48;
+  // three independent 16-byte loads spread over three lanes
+  int4 vi = make_int4(0, 0, 0, 0), vd = make_int4(0, 0, 0, 0);
+  int2 o = make_int2(0, 0);
+  if (lane == 0) vi = __ldg(&G.vi[c]);
+  if (lane == 1) o = __ldg(&G.off[c]);
+  if (lane == 2) vd = __ldg(&G.vdir[c]);
+  const int32_t dout = __shfl_sync(kFull, vi.y, 0), din = __shfl_sync(kFull, vi.z, 0);
+  const int32_t oo = __shfl_sync(kFull, o.x, 1), oi = __shfl_sync(kFull, o.y, 1);
+  int4 d;
+  d.x = __shfl_sync(kFull, vd.x, 2);
+  d.y = __shfl_sync(kFull, vd.y, 2);
+  d.z = __shfl_sync(kFull, vd.z, 2);
+  d.w = __shfl_sync(kFull, vd.w, 2);
+  if (lane == 0) {
+    S.map[pos] = c;
+    S.deg_out[pos] = dout;
+    S.deg_in[pos] = din;
+    S.off_out[pos] = oo;
+    S.off_in[pos] = oi;
+    S.dir[pos] = d;
+  }
+}
+
+// Find the group (arc label, vertex label) in a directory span; {first, length} or {0, 0}.
+template <bool kC>
+__device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t first, int32_t cnt,
+                                           int32_t alab, int32_t vlab, int lane, uint64_t &ctr) {
+  for (int32_t b = 0; b < cnt; b += 32) {
+    int4 e = make_int4(0, 0, 0, 0);
+    bool hit = false;
+    if (b + lane < cnt) {
+      if (kC) ctr += 16;
+      e = __ldg(dir + first + b + lane);
+      hit = e.x == alab && e.y == vlab;
+    }
+    const uint32_t m = __ballot_sync(kFull, hit);
+    if (m) {
+      const int src = __ffs(m) - 1;
+      const int32_t s0 = __shfl_sync(kFull, e.z, src), s1 = __shfl_sync(kFull, e.w, src);
+      return make_int2(s0, s1 - s0);
+    }
+  }
+  return make_int2(0, 0);
+}
+
+// Look up the label group of every anchor of position p; unless `keep`, pick the
+// smallest group as the driving range.
+template <bool kC>
+__device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, WarpState &S,
+                                            int2 *__restrict__ grp, int p, int lane, bool keep,
+                                            uint64_t &ctr) {
+  int best = 0;
+  int32_t best_len = INT32_MAX;
+  for (int j = 0; j < P.npos[p]; ++j) {
+    const Cons cs = P.cons[p][j];
+    const int4 d = S.dir[cs.q];
+    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G.gdir_out, d.x, d.y, cs.lab, P.vlab[p], lane, ctr)
+                                   : dir_lookup<kC>(G.gdir_in, d.z, d.w, cs.lab, P.vlab[p], lane, ctr);
+    if (lane == 0) grp[P.gbase[p] + j] = r;
+    if (r.y < best_len) {
+      best_len = r.y;
+      best = j;
+    }
+  }
+  if (lane == 0 && !keep) {
+    const Cons cs = P.cons[p][best];
+    const int2 r = grp[P.gbase[p] + best];
+    const int32_t lo = (cs.kind == kOut ? S.off_out[cs.q] : S.off_in[cs.q]) + r.x;
+    S.drive[p] = best;
+    S.lo[p] = lo;
+    S.hi[p] = lo + r.y;
+    S.mask[p] = 0;
+  }
+}
+
+// Does candidate c (taken from the driving group, so its arc label and vertex
+// label already match) satisfy every other condition of position p?
+template <bool kC>
+__device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P,
+                                                const WarpState &S, const int2 *__restrict__ grp,
+                                                int p, int drive, int32_t c, bool leaf,
+                                                const uint8_t *root_mask, uint64_t &ctr) {
+  for (int i = 0; i < p; ++i)
+    if (S.map[i] == c) return false;                        // injective
+  if (root_mask && p == P.root_pos && !root_mask[c]) return false;
+  const int nc = P.ncons[p];
+  // c's own degrees and offsets: needed for the degree filter (inner levels) and
+  // to search c's shorter list instead of a hub's
+  const bool need_c = !leaf || nc > 1;
+  int4 vi = make_int4(0, 0, 0, 0);
+  int2 oc = make_int2(0, 0);
+  if (need_c) {
+#if HM_EAGER_OFFSETS
+    // both records in flight together (the offsets are used by most searches)
+    if (kC) ctr += nc > 1 ? 32 : 16;
+    vi = __ldg(&G.vi[c]);
+    if (nc > 1) oc = __ldg(&G.off[c]);
+    if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
+#else
+    if (kC) ctr += 16;
+    vi = __ldg(&G.vi[c]);
+    if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
+    if (kC && nc > 1) ctr += 16;
+    if (nc > 1) oc = __ldg(&G.off[c]);
+#endif
+  }
+  for (int j = 0; j < nc; ++j) {
+    if (j == drive) continue;
+    const Cons cs = P.cons[p][j];
+    const int q = cs.q;
+    const int32_t fq = S.map[q];
+    const bool fwd = cs.kind == kOut || cs.kind == kNotOut;   // arc f(q) -> c ?
+    bool found;
+    if (cs.kind <= kIn) {
+      // positive: c in the (label, label) group of f(q), or f(q) in c's reverse list
+      const int2 r = grp[P.gbase[p] + j];
+      const int32_t rev_len = fwd ? vi.z : vi.y;
+      if (r.y == 0) return false;
+      if (rev_len < r.y) {
+        const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
+                              : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
+        if (kC && i >= 0) ctr += 4;
+        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+      } else {
+        const int32_t base = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
+        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, base, r.y, c, ctr) >= 0;
+      }
+      if (!found) return false;
+    } else {
+      // induced: no arc at all between f(q) and c in this direction
+      const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
+      const int32_t lb = fwd ? vi.z : vi.y;
+      if (la == 0 || lb == 0) continue;
+      if (la <= lb) {
+        found = search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) >= 0;
+      } else {
+        found = search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) >= 0;
+      }
+      if (found) return false;
+    }
+  }
+  return true;
+}
+
+// One condition j of position p on candidate c (the j-th entry of cons[p]).
+// The lane with `base` set also applies the per-candidate checks
+// (injectivity, root mask, degree filter on inner levels).
+template <bool kC>
+__device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, const WarpState &S,
+                                          const int2 *__restrict__ grp, int p, int j, int32_t c,
+                                          bool base, bool leaf, const uint8_t *root_mask,
+                                          uint64_t &ctr) {
+  if (base) {
+    for (int i = 0; i < p; ++i)
+      if (S.map[i] == c) return false;
+    if (root_mask && p == P.root_pos && !root_mask[c]) return false;
+  }
+  if (kC) ctr += 16;
+  const int4 vi = __ldg(&G.vi[c]);
+  if (base && !leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
+  const Cons cs = P.cons[p][j];
+  const int q = cs.q;
+  const int32_t fq = S.map[q];
+  const bool fwd = cs.kind == kOut || cs.kind == kNotOut;
+  if (cs.kind <= kIn) {
+    const int2 r = grp[P.gbase[p] + j];
+    const int32_t rev_len = fwd ? vi.z : vi.y;
+    if (r.y == 0 || rev_len == 0) return false;
+    if (rev_len < r.y) {
+      if (kC) ctr += 16;
+      const int2 oc = __ldg(&G.off[c]);
+      const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
+                            : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
+      if (kC && i >= 0) ctr += 4;
+      return i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+    }
+    const int32_t lo = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
+    return search_c<kC>(fwd ? G.gout_adj : G.gin_adj, lo, r.y, c, ctr) >= 0;
+  }
+  const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
+  const int32_t lb = fwd ? vi.z : vi.y;
+  if (la == 0 || lb == 0) return true;
+  if (la <= lb)
+    return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
+  if (kC) ctr += 16;
+  const int2 oc = __ldg(&G.off[c]);
+  return search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) < 0;
+}
+
+// ---- bounded lock-free queue (Vyukov-style sequence numbers) --------------
+
+__device__ bool q_push(const ExtArgs &A, WarpState &S, int lane) {
+  long long pos = -1;
+  if (lane == 0) {
+    atomic_u64 tail(A.ctl->tail);
+    unsigned long long p = tail.load(cuda::memory_order_relaxed);
+    for (int it = 0; it < 64; ++it) {
+      atomic_u64 seq(A.qseq[p & (kQueueCap - 1)]);
+      unsigned long long sq = seq.load(cuda::memory_order_acquire);
+      long long dif = (long long)sq - (long long)p;
+      if (dif == 0) {
+        if (tail.compare_exchange_strong(p, p + 1, cuda::memory_order_relaxed)) {
+          pos = (long long)p;
+          break;
+        }
+      } else if (dif < 0) {
+        break;  // full
+      } else {
+        p = tail.load(cuda::memory_order_relaxed);
+      }
+    }
+  }
+  pos = __shfl_sync(kFull, pos, 0);
+  if (pos < 0) return false;
+  Task *dst = A.qbuf + (pos & (kQueueCap - 1));
+  if (lane < kTaskWords) reinterpret_cast<int32_t *>(dst)[lane] = reinterpret_cast<const int32_t *>(&S.stage)[lane];
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) {
+    atomic_u64 seq(A.qseq[pos & (kQueueCap - 1)]);
+    seq.store((unsigned long long)pos + 1, cuda::memory_order_release);
+  }
+  return true;
+}
+
+__device__ bool q_pop(const ExtArgs &A, WarpState &S, int lane) {
+  long long pos = -1;
+  if (lane == 0) {
+    atomic_u64 head(A.ctl->head);
+    unsigned long long p = head.load(cuda::memory_order_relaxed);
+    for (int it = 0; it < 64; ++it) {
+      atomic_u64 seq(A.qseq[p & (kQueueCap - 1)]);
+      unsigned long long sq = seq.load(cuda::memory_order_acquire);
+      long long dif = (long long)sq - (long long)(p + 1);
+      if (dif == 0) {
+        if (head.compare_exchange_strong(p, p + 1, cuda::memory_order_relaxed)) {
+          pos = (long long)p;
+          break;
+        }
+      } else if (dif < 0) {
+        break;  // empty (or the producer has not published yet)
+      } else {
+        p = head.load(cuda::memory_order_relaxed);
+      }
+    }
+    if (pos >= 0) __threadfence();
+  }
+  pos = __shfl_sync(kFull, pos, 0);
+  __syncwarp();
+  if (pos < 0) return false;
+  const Task *src = A.qbuf + (pos & (kQueueCap - 1));
+  if (lane < kTaskWords)
+    reinterpret_cast<int32_t *>(&S.stage)[lane] = ((const volatile int32_t *)src)[lane];
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) {
+    atomic_u64 seq(A.qseq[pos & (kQueueCap - 1)]);
+    seq.store((unsigned long long)pos + kQueueCap, cuda::memory_order_release);
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool queue_maybe_nonempty(const ExtArgs &A) {
+  atomic_u64 head(A.ctl->head), tail(A.ctl->tail);
+  return tail.load(cuda::memory_order_acquire) > head.load(cuda::memory_order_acquire);
+}
+
+// Split the shallowest unfinished range (or pending chunk) and donate one part.
+// The task being run may restrict its first chunk [first_lo, first_lo + 32) at
+// depth L0 to the candidates in first_mask; a split of that window hands the
+// shifted restriction to the new task (such tasks never extend past the window).
+__device__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0, int level,
+                           int lane, int32_t first_lo, uint32_t first_mask, int32_t pid) {
+  int l = -1, kind = 0;
+  for (int d = L0; d <= level; ++d) {
+    if (S.hi[d] - S.lo[d] >= A.split_min) { l = d; kind = 0; break; }
+    if (d < level && __popc(S.mask[d]) >= 2) { l = d; kind = 1; break; }
+  }
+  if (l < 0) return false;
+  if (lane == 0) {
+    Task &t = S.stage;
+    t.depth = l;
+    t.drive = S.drive[l];
+    t.pid = pid;
+    t.pad[0] = t.pad[1] = 0;
+    for (int i = 0; i < kMaxK; ++i) t.map[i] = i < l ? S.map[i] : -1;
+    if (kind == 0) {
+      const int32_t mid = S.lo[l] + ((S.hi[l] - S.lo[l]) >> 1);
+      t.lo = mid;
+      t.hi = S.hi[l];
+      t.pmask = kFull;
+      if (l == L0 && first_mask != kFull && mid >= first_lo && mid < first_lo + 32)
+        t.pmask = first_mask >> (mid - first_lo);
+    } else {
+      uint32_t m = S.mask[l];
+      int keep = __popc(m) >> 1;
+      uint32_t mine = 0;
+      for (int i = 0; i < keep; ++i) {
+        uint32_t low = m & (0u - m);
+        mine |= low;
+        m ^= low;
+      }
+      t.lo = S.base[l];
+      t.hi = S.base[l] + 32;
+      t.pmask = m;  // the upper half goes away
+      S.mask[l] = mine;
+    }
+  }
+  __syncwarp();
+  bool pushed = q_push(A, S, lane);
+  if (lane == 0) {
+    if (pushed) {
+      if (kind == 0) S.hi[l] = S.stage.lo;
+      atomicAdd(&A.ctl->donated, 1ull);
+    } else if (kind == 1) {
+      S.mask[l] |= S.stage.pmask;  // could not donate: keep the work
+    }
+  }
+  __syncwarp();
+  return pushed;
+}
+
+__host__ __device__ constexpr size_t warp_smem_bytes(int ngrp) {
+  return (sizeof(WarpState) + sizeof(int2) * (size_t)ngrp + 15) / 16 * 16;
+}
+
+template <bool kRows, bool kC, int kMinBlocks, bool kBatch>
+__global__ void __launch_bounds__(kExtThreads, kMinBlocks)
+k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
+         const __grid_constant__ ExtArgs A) {
+  uint64_t ctr = 0, lanes = 0;
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const int lane = threadIdx.x & 31;
+  const size_t stride = warp_smem_bytes(kBatch ? A.grp_slots : P0.ngrp);
+  WarpState &S = *reinterpret_cast<WarpState *>(s_raw + (threadIdx.x >> 5) * stride);
+  int2 *grp = reinterpret_cast<int2 *>(s_raw + (threadIdx.x >> 5) * stride + sizeof(WarpState));
+  const unsigned long long deadline = globaltimer_ns() + A.budget_ns;
+  const unsigned long long nseeds = *A.nseeds;
+  unsigned long long my_count = 0, my_chunks = 0;
+  unsigned long long seed_at = 0, seed_end = 0;  // this warp's claimed seeds
+  int32_t requests_seen = 0, status_seen = kStatOk;  // lane 0: values from the previous poll
+  bool seeds_done = false, stop = false;
+  if (lane == 0) atomicAdd(&A.ctl->active, 1);
+
+  while (!stop) {
+    // ---------------- acquire a task ----------------
+    int got = 0;  // 1 seed, 2 donated
+    int32_t pid = 0;
+    if (!seeds_done) {
+      if (seed_at >= seed_end) {
+        unsigned long long s0 = 0;
+        if (lane == 0) s0 = atomicAdd(&A.ctl->seed_next, (unsigned long long)A.seeds_per_fetch);
+        seed_at = __shfl_sync(kFull, s0, 0);
+        seed_end = min(seed_at + (unsigned long long)A.seeds_per_fetch, nseeds);
+      }
+      const unsigned long long s = seed_at++;
+      if (s < seed_end) {
+        const int2 uv = A.seeds[s];
+        if (kBatch) pid = A.seed_pid[s];
+        if (kC && lane == 0) ctr += kBatch ? 12 : 8;
+        set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
+        set_mapped<kC>(G, S, 1, uv.y, lane, ctr);
+        __syncwarp();
+        got = 1;
+      } else {
+        seeds_done = true;
+      }
+    }
+    if (!got && q_pop(A, S, lane)) got = 2;
+    if (!got) {
+      // go idle: advertise, and wait for a donation or for global quiescence
+      if (lane == 0) {
+        atomicAdd(&A.ctl->hungry, 1);
+        atomicAdd(&A.ctl->requests, 1);
+        atomicSub(&A.ctl->active, 1);
+      }
+      unsigned ns = 64;
+      for (;;) {
+        int quit = 0;
+        if (lane == 0) {
+          if (ld_volatile(&A.ctl->status) != kStatOk) quit = 1;
+          else if (globaltimer_ns() > deadline) {
+            atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
+            quit = 1;
+          } else {
+            __threadfence();
+            int32_t act = ld_volatile(&A.ctl->active);
+            __threadfence();
+            if (act == 0 && !queue_maybe_nonempty(A)) quit = 1;
+          }
+          if (!quit && queue_maybe_nonempty(A)) {
+            atomicAdd(&A.ctl->active, 1);
+            quit = 2;  // try to take it
+          }
+        }
+        quit = __shfl_sync(kFull, quit, 0);
+        if (quit == 1) { stop = true; break; }
+        if (quit == 2) {
+          if (q_pop(A, S, lane)) {
+            got = 2;
+            if (lane == 0) atomicSub(&A.ctl->hungry, 1);
+            break;
+          }
+          if (lane == 0) atomicSub(&A.ctl->active, 1);
+        }
+        __nanosleep(ns);
+        ns = min(ns * 2, 4096u);
+      }
+      if (stop) {
+        if (lane == 0) atomicSub(&A.ctl->hungry, 1);
+        break;
+      }
+    }
+    if (got == 2 && kBatch) pid = S.stage.pid;
+    const Plan &P = kBatch ? A.plans[pid] : P0;
+    const int k = P.k;
+    unsigned long long *const row_cursor = kBatch ? A.row_cursor + pid : &A.ctl->rows_written;
+    int32_t *const row_base = kBatch ? A.rows + A.row_off[pid] : A.rows;
+    const unsigned long long row_cap = kBatch ? A.row_cap[pid] : A.cap;
+    unsigned long long task_count = 0;
+    if (got == 1) {
+      if (kBatch && k == 2) {
+        // a two-vertex pattern: the validated seed is the whole match
+        if (lane == 0) {
+          atomicAdd(&A.counts[pid], 1ull);
+          if (kRows) {
+            const unsigned long long r = atomicAdd(row_cursor, 1ull);
+            if (r < row_cap) {
+              row_base[r * 2 + P.orig[0]] = S.map[0];
+              row_base[r * 2 + P.orig[1]] = S.map[1];
+            }
+          }
+        }
+        __syncwarp();
+        continue;
+      }
+      setup_level<kC>(G, P, S, grp, 2, lane, false, ctr);
+    }
+    int L0 = 2;
+    uint32_t first_mask = kFull;
+    int32_t first_lo = -1;
+    if (got == 2) {
+      // install a donated task
+      const int d = S.stage.depth;
+      for (int i = 0; i < d; ++i) set_mapped<kC>(G, S, i, S.stage.map[i], lane, ctr);
+      __syncwarp();
+      setup_level<kC>(G, P, S, grp, d, lane, true, ctr);
+      if (lane == 0) {
+        S.drive[d] = S.stage.drive;
+        S.lo[d] = S.stage.lo;
+        S.hi[d] = S.stage.hi;
+        S.mask[d] = 0;
+      }
+      __syncwarp();
+      L0 = d;
+      first_mask = S.stage.pmask;
+      first_lo = S.stage.lo;
+    }
+    __syncwarp();
+
+    // ---------------- depth-first extension ----------------
+    int level = L0;
+    while (true) {
+      if (S.mask[level] == 0) {
+        const int32_t lo = S.lo[level];
+        int32_t hi = S.hi[level];
+        if (lo >= hi) {
+          if (level == L0) break;
+          --level;
+          continue;
+        }
+        ++my_chunks;
+        if ((my_chunks & 63) == 0) {
+          // budget check; the status word read here was requested 64 chunks
+          // ago, so its latency is hidden behind that work
+          int halt = 0;
+          if (lane == 0) {
+            const int32_t status = status_seen;
+            status_seen = ld_volatile(&A.ctl->status);
+            if (status != kStatOk) halt = 1;
+            else if (globaltimer_ns() > deadline) {
+              atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
+              halt = 1;
+            } else if (A.max_chunks) {
+              unsigned long long tot = atomicAdd(&A.ctl->chunks, 64ull) + 64;
+              if (tot > A.max_chunks) {
+                atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
+                halt = 1;
+              }
+            } else {
+              atomicAdd(&A.ctl->chunks, 64ull);
+            }
+          }
+          if (__shfl_sync(kFull, halt, 0)) { stop = true; break; }
+        }
+        if ((my_chunks & A.poll_mask) == 0) {
+          // donate only while fewer tasks wait in the queue than warps wait
+          // for work; the idle-warp count used is the one requested at the
+          // previous poll, so the poll does not stall the warp
+          int want = 0;
+          if (lane == 0) {
+            const int32_t asked = requests_seen;
+            requests_seen = ld_volatile(&A.ctl->requests);
+            // claim one outstanding request: one donation per idle warp's ask
+            if (asked > 0) want = atomicSub(&A.ctl->requests, 1) > 0 ? 1 : 2;
+          }
+          want = __shfl_sync(kFull, want, 0);
+          if (want) {
+            bool gave = false;
+            if (want == 1) {
+              gave = try_donate(A, P, S, L0, level, lane, first_lo, first_mask, pid);
+              hi = S.hi[level];  // a split of this level keeps [lo, mid)
+            }
+            if (lane == 0 && !gave) atomicAdd(&A.ctl->requests, 1);  // not claimed / nothing to give
+          }
+        }
+        const int drive = S.drive[level];
+        const Cons dc = P.cons[level][drive];
+        const int32_t *adj = dc.kind == kOut ? G.gout_adj : G.gin_adj;
+        uint32_t allow = kFull;
+        if (level == L0 && first_mask != kFull && lo >= first_lo && lo < first_lo + 32)
+          allow = first_mask >> (lo - first_lo);
+        const bool leaf = level == k - 1;
+        const int J = P.ncons[level] - 1;  // conditions besides the driving one
+        bool ok = false;
+        int32_t c = -1;
+        uint32_t m;
+        int take;
+        if (A.pair_mode && J >= 2 && (hi - lo) * J <= 32) {
+          // the whole range fits one round of (candidate, condition) pairs:
+          // a candidate's searches run side by side instead of one after another
+          take = (int)(hi - lo);
+          const int ci = lane / J, slot = lane - ci * J;
+          bool pass = false;
+          if (ci < take && ((allow >> ci) & 1u)) {
+            const int32_t cc = __ldg(adj + lo + ci);
+            if (kC && slot == 0) {
+              ctr += 4;
+              ++lanes;
+            }
+            pass = check_one<kC>(G, P, S, grp, level, slot < drive ? slot : slot + 1, cc, slot == 0,
+                                 leaf, A.root_mask, ctr);
+          }
+          const uint32_t bal = __ballot_sync(kFull, pass);
+          const uint32_t need = (1u << J) - 1u;
+          m = 0;
+          for (int i = 0; i < take; ++i)
+            if (((bal >> (i * J)) & need) == need) m |= 1u << i;
+          if (lane < take && ((m >> lane) & 1u)) {
+            ok = true;
+            c = __ldg(adj + lo + lane);
+          }
+        } else {
+          take = 32;
+          const int32_t idx = lo + lane;
+          if (idx < hi && ((allow >> lane) & 1u)) {
+            c = __ldg(adj + idx);
+            if (kC) {
+              ctr += 4;
+              ++lanes;
+            }
+            ok = check_candidate<kC>(G, P, S, grp, level, drive, c, leaf, A.root_mask, ctr);
+          }
+          m = __ballot_sync(kFull, ok);
+        }
+        if (lane == 0) S.lo[level] = lo + take;
+        if (leaf) {
+          // leaf: every survivor is a match
+          const int nm = __popc(m);
+          task_count += nm;
+          if (kRows && nm) {
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(row_cursor, (unsigned long long)nm);
+            at = __shfl_sync(kFull, at, 0);
+            if (ok) {
+              unsigned long long r = at + __popc(m & lanemask_lt());
+              if (r < row_cap) {
+                if (kC) ctr += 4 * k;
+                int32_t *row = row_base + r * k;
+                for (int i = 0; i < k - 1; ++i) row[P.orig[i]] = S.map[i];
+                row[P.orig[k - 1]] = c;
+              }
+            }
+          }
+          __syncwarp();
+          continue;
+        }
+        if (lane == 0) {
+          S.mask[level] = m;
+          S.base[level] = lo;
+        }
+        __syncwarp();
+        continue;
+      }
+      // descend into the next pending survivor
+      const uint32_t m = S.mask[level];
+      const int b = __ffs(m) - 1;
+      const Cons dc = P.cons[level][S.drive[level]];
+      const int32_t *adj = dc.kind == kOut ? G.gout_adj : G.gin_adj;
+      const int32_t c = __ldg(adj + S.base[level] + b);
+      __syncwarp();
+      if (lane == 0) S.mask[level] = m & (m - 1);
+      if (kC && lane == 0) ctr += 4;
+      set_mapped<kC>(G, S, level, c, lane, ctr);
+      __syncwarp();
+      ++level;
+      setup_level<kC>(G, P, S, grp, level, lane, false, ctr);
+      __syncwarp();
+    }
+    if (kBatch) {
+      if (lane == 0 && task_count) atomicAdd(&A.counts[pid], task_count);
+    } else {
+      my_count += task_count;
+    }
+  }
+  if (lane == 0) {
+    if (!stop) atomicSub(&A.ctl->active, 1);
+    if (my_count) atomicAdd(&A.ctl->count, my_count);
+    if (my_chunks & 63) atomicAdd(&A.ctl->chunks, my_chunks & 63);
+  }
+  if (kC) {
+    for (int o = 16; o; o >>= 1) {
+      ctr += __shfl_xor_sync(kFull, ctr, o);
+      lanes += __shfl_xor_sync(kFull, lanes, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.ctl->bytes_extend, (unsigned long long)ctr);
+      atomicAdd(&A.ctl->lanes, (unsigned long long)lanes);
+    }
+  }
+}
+
+// two-vertex patterns: every seed is a match
+__global__ void k_seed_rows(const __grid_constant__ Plan P, const int2 *__restrict__ seeds,
+                            const unsigned long long *__restrict__ nseeds, int32_t *__restrict__ rows,
+                            unsigned long long cap, Ctl *ctl) {
+  const unsigned long long n = *nseeds;
+  for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < n;
+       s += (unsigned long long)gridDim.x * blockDim.x) {
+    if (rows && s < cap) {
+      int2 uv = seeds[s];
+      rows[s * 2 + P.orig[0]] = uv.x;
+      rows[s * 2 + P.orig[1]] = uv.y;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->count = n;
+}
+
+__global__ void k_qinit(unsigned long long *seq) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < kQueueCap;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    seq[i] = i;
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+
+struct Timer {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaStream_t s;
+  bool on;
+  Timer(cudaStream_t st, bool enabled) : s(st), on(enabled) {
+    if (on) {
+      cudaEventCreate(&ev[0]);
+      cudaEventCreate(&ev[1]);
+      cudaEventRecord(ev[0], s);
+    }
+  }
+  void stop() {
+    if (on) cudaEventRecord(ev[1], s);
+  }
+  // Elapsed time; call only after the stream has been synchronised.
+  float ms() {
+    float t = 0.f;
+    if (on && cudaEventQuery(ev[1]) == cudaSuccess) cudaEventElapsedTime(&t, ev[0], ev[1]);
+    return t;
+  }
+  ~Timer() {
+    if (on) {
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+    }
+  }
+};
+
+// Stream-ordered temporaries of one call, freed (stream-ordered) when it ends.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void *> p;
+  explicit Scratch(cudaStream_t st) : s(st) { p.reserve(16); }
+  cudaError_t get(void **out, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(out, bytes ? bytes : 16, s);
+    if (e == cudaSuccess) p.push_back(*out);
+    return e;
+  }
+  ~Scratch() {
+    for (void *q : p) cudaFreeAsync(q, s);
+  }
+};
+
+using ExtendKernel = void (*)(DevGraph, Plan, ExtArgs);
+
+// Occupancy variants: resident 256-thread blocks per SM requested from the
+// compiler (it caps registers per thread accordingly).
+constexpr int kMinBlockChoices[3] = {5, 6, 8};
+
+int min_blocks_slot(int min_blocks) {
+  for (int i = 0; i < 3; ++i)
+    if (kMinBlockChoices[i] == min_blocks) return i;
+  return 0;
+}
+
+template <bool R, bool C, bool B>
+ExtendKernel extend_kernel_mb(int slot) {
+  switch (slot) {
+    case 1: return k_extend<R, C, 6, B>;
+    case 2: return k_extend<R, C, 8, B>;
+    default: return k_extend<R, C, 5, B>;
+  }
+}
+
+template <bool B = false>
+ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0) {
+  if (rows)
+    return counters ? extend_kernel_mb<true, true, B>(slot) : extend_kernel_mb<true, false, B>(slot);
+  return counters ? extend_kernel_mb<false, true, B>(slot) : extend_kernel_mb<false, false, B>(slot);
+}
+
+// Resident blocks of an extension kernel variant for a dynamic shared-memory size.
+template <bool B = false>
+int extend_grid(bool rows, bool counters, size_t smem, int slot = 0) {
+  static int cache[3][4][64] = {};
+  const int sm = (int)std::min<size_t>(smem / 1024, 63);
+  int &c = cache[slot][(rows ? 2 : 0) + (counters ? 1 : 0)][sm];
+  if (!c) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, extend_kernel<B>(rows, counters, slot), kExtThreads, smem);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    c = std::max(per_sm, 1) * num_sms();
+  }
+  return c;
+}
+
+}  // namespace
+}  // namespace hm

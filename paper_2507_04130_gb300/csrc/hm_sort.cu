@@ -29,7 +29,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 4;
 constexpr int kTile = kSortThreads * kItems;
-constexpr int kMaxKeyCols = 16;
+constexpr int kMaxKeyCols = 17;
 
 struct KeySpec {
   int ncols;                 // key columns
@@ -200,6 +200,7 @@ ScatterFn scatter_for(int width) {
     case 14: return launch_scatter<14>;
     case 15: return launch_scatter<15>;
     case 16: return launch_scatter<16>;
+    case 17: return launch_scatter<17>;
     default: return nullptr;
   }
 }
