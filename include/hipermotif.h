@@ -213,6 +213,50 @@ hm_status hm_enumerate_batch(const hm_graph *g, const hm_pattern *const *pattern
                              const int32_t *modes, int32_t npat, int32_t *rows_dev,
                              const uint64_t *row_offsets, uint64_t *counts, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Query server over one resident graph (continuous batching).
+ *
+ * hm_server_create -- starts `nslots` dispatcher slots (host threads, each
+ * with its own CUDA stream) serving queries against g, which must outlive the
+ * server.  A free slot takes every waiting query that the device-memory
+ * budget admits, up to max_batch, and runs them as one batch
+ * (hm_count_batch, then hm_enumerate_batch for the queries that want rows);
+ * queries that arrive meanwhile join the next free slot's batch, and batches
+ * of different slots overlap on the GPU.  Admission: each query reserves
+ * 24 B x m (its worst-case seed queues) + 8 MiB while it runs; rows are
+ * reserved from the count before enumeration, and a query whose rows do not
+ * fit the remaining budget gets its count only (rows_dropped = 1).
+ *   mem_budget  device bytes for admitted queries (0 = twice what max_batch
+ *               queries per slot reserve, the second half for their rows);
+ *               HM_ERR_ARG if it cannot admit one query.
+ * hm_server_submit -- validates and reorders the pattern (as hm_load_pattern,
+ *   HOST arrays), queues it and returns its id at once.  mode HM_MONO or
+ *   HM_INDUCED; want_rows 0/1.  Thread-safe.
+ * hm_server_poll -- done = 1 once the query has completed (wait = 1 blocks
+ *   until then).  When done: *count, *latency_ms (submit to completion, host
+ *   clock), *rows_dropped, and *rows / *nrows: HOST rows (nrows x k int32,
+ *   sorted) owned by the server until hm_server_release.  Returns the query's
+ *   status (HM_OK, or the error its batch met).
+ * hm_server_release -- frees a completed query's results.
+ * hm_server_stats -- batches launched, queries completed, the largest number
+ *   of batches that were in flight at once, queries whose rows were dropped.
+ * hm_server_destroy -- serves what is queued, joins the slots, frees all.
+ * ------------------------------------------------------------------------ */
+typedef struct hm_server hm_server;
+
+hm_status hm_server_create(const hm_graph *g, int32_t nslots, int32_t max_batch,
+                           uint64_t mem_budget, hm_server **out);
+hm_status hm_server_submit(hm_server *s, int32_t k, int32_t mp, const int32_t *src,
+                           const int32_t *dst, const int32_t *vlab, const int32_t *elab,
+                           int32_t mode, int32_t want_rows, uint64_t *qid);
+hm_status hm_server_poll(hm_server *s, uint64_t qid, int32_t wait, int32_t *done, uint64_t *count,
+                         double *latency_ms, int32_t *rows_dropped, const int32_t **rows,
+                         uint64_t *nrows);
+hm_status hm_server_release(hm_server *s, uint64_t qid);
+hm_status hm_server_stats(hm_server *s, uint64_t *batches, uint64_t *completed,
+                          uint64_t *max_inflight_batches, uint64_t *rows_dropped);
+void hm_server_destroy(hm_server *s);
+
 /* hm_injected_states -- the depth-2 states the edge scan produces: every
  * target arc accepted by the vertex validator (Alg. 2) and the edge
  * validator (Alg. 3) for the reordered arc between positions 0 and 1, as
@@ -289,6 +333,19 @@ typedef struct {
 
 hm_status hm_set_tuning(const hm_tuning *t);
 hm_status hm_get_tuning(hm_tuning *t);
+
+/* hm_autotune -- picks the knobs above for a workload: it times the batched
+ * count (hm_count_batch) of the given patterns under candidate settings
+ * (blocks per SM 5/6, split threshold 64/512, pair mode 0/1, poll interval
+ * 32/128/512, seeds per fetch 1/2, and the current setting), best of two runs
+ * each, until budget_ms of wall time is spent (0 = try all), installs the
+ * fastest with hm_set_tuning and returns it in *best (and its time in
+ * *best_ms, may be NULL).  Every run's counts are compared with the first
+ * run's; a difference (which no knob can cause) restores the previous
+ * setting and returns HM_ERR_CUDA.  Synchronous. */
+hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *patterns, const int32_t *modes,
+                      int32_t npat, uint32_t budget_ms, hm_tuning *best, float *best_ms,
+                      void *stream);
 
 /* ------------------------------------------------------------------------
  * Statistics of the calling thread's last matching call (host struct).

@@ -26,7 +26,7 @@ from .binding import HM_MONO as MONO
 from .binding import HMError, check, lib
 
 __all__ = ["Graph", "Pattern", "count_matches", "enumerate_matches", "count_matches_rooted",
-           "count_matches_part", "enumerate_matches_part", "count_batch", "enumerate_batch",
+           "count_matches_part", "enumerate_matches_part", "count_batch", "enumerate_batch", "autotune", "Server",
            "injected_states", "set_budget", "set_timing", "set_counters", "set_tuning", "get_tuning",
            "last_stats", "MONO", "INDUCED",
            "HMError", "binding"]
@@ -246,6 +246,87 @@ def enumerate_batch(g: Graph, patterns, modes, counts=None, stream=None) -> list
                                 ctypes.c_void_p(got.ctypes.data), _stream_ptr(stream))
     check(st, "hm_enumerate_batch")
     return [buf[int(offs[i]): int(offs[i + 1])].view(int(got[i]), ks[i]) for i in range(n)]
+
+
+def autotune(g: Graph, patterns, modes, budget_ms: int = 2000, stream=None) -> dict:
+    """Time candidate launch knobs on the batched count of `patterns`; install and return the best."""
+    n, handles, m = _batch_args(patterns, modes)
+    t = binding.hm_tuning()
+    ms = ctypes.c_float()
+    check(lib.hm_autotune(g.handle, ctypes.cast(handles, ctypes.c_void_p), _ptr(m), n, int(budget_ms),
+                          ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)), "hm_autotune")
+    out = t.as_dict()
+    out["ms"] = float(ms.value)
+    return out
+
+
+class Server:
+    """Query server over one resident graph (hm_server_*): submit from any thread, poll for results.
+
+    `slots` dispatcher slots (each a host thread with its own stream) batch the
+    waiting queries that the device-memory budget admits; batches of different
+    slots overlap on the GPU.
+    """
+
+    def __init__(self, g: Graph, slots: int = 4, max_batch: int = 64, mem_budget: int = 0):
+        h = ctypes.c_void_p()
+        check(lib.hm_server_create(g.handle, int(slots), int(max_batch), int(mem_budget), ctypes.byref(h)),
+              "hm_server_create")
+        self._h = h
+        self._g = g  # the graph must outlive the server
+        self._k = {}
+
+    def submit(self, pattern, mode: int, want_rows: bool = True) -> int:
+        arrays = [_host_i32(a) for a in (pattern.src, pattern.dst, pattern.vlab, pattern.elab)]
+        qid = ctypes.c_uint64()
+        check(lib.hm_server_submit(self._h, int(pattern.k), int(arrays[0].shape[0]), *[_ptr(a) for a in arrays],
+                                   int(mode), 1 if want_rows else 0, ctypes.byref(qid)), "hm_server_submit")
+        self._k[int(qid.value)] = int(pattern.k)
+        return int(qid.value)
+
+    def result(self, qid: int, wait: bool = True):
+        """None while pending; else dict(count, latency_ms, rows_dropped, rows: numpy [n, k] or None).
+
+        A completed query's results are copied out and released on the server.
+        """
+        done = ctypes.c_int32()
+        cnt = ctypes.c_uint64()
+        lat = ctypes.c_double()
+        dropped = ctypes.c_int32()
+        rows = ctypes.POINTER(ctypes.c_int32)()
+        nrows = ctypes.c_uint64()
+        st = lib.hm_server_poll(self._h, int(qid), 1 if wait else 0, ctypes.byref(done), ctypes.byref(cnt),
+                                ctypes.byref(lat), ctypes.byref(dropped), ctypes.byref(rows),
+                                ctypes.byref(nrows))
+        if not done.value:
+            check(st, "hm_server_poll")
+            return None
+        k = self._k.pop(int(qid))
+        out = {"count": int(cnt.value), "latency_ms": float(lat.value), "rows_dropped": bool(dropped.value),
+               "rows": None}
+        n = int(nrows.value)
+        if n:
+            out["rows"] = np.ctypeslib.as_array(rows, shape=(n * k,)).copy().reshape(n, k)
+        check(lib.hm_server_release(self._h, int(qid)), "hm_server_release")
+        check(st, "hm_server_poll")
+        return out
+
+    def stats(self) -> dict:
+        v = [ctypes.c_uint64() for _ in range(4)]
+        check(lib.hm_server_stats(self._h, *[ctypes.byref(x) for x in v]), "hm_server_stats")
+        return dict(zip(["batches", "completed", "max_inflight_batches", "rows_dropped"],
+                        [int(x.value) for x in v]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def count_matches_rooted(g: Graph, p: Pattern, mode: int, root: int, mask, stream=None) -> int:

@@ -25,7 +25,9 @@ EXPORTED = [
     "hm_enumerate_matches", "hm_count_matches_rooted", "hm_count_matches_part",
     "hm_enumerate_matches_part", "hm_injected_states", "hm_set_budget",
     "hm_last_stats", "hm_set_timing", "hm_set_counters", "hm_count_matches_static",
-    "hm_set_tuning", "hm_get_tuning", "hm_count_batch", "hm_enumerate_batch",
+    "hm_set_tuning", "hm_get_tuning", "hm_count_batch", "hm_enumerate_batch", "hm_autotune",
+    "hm_server_create", "hm_server_submit", "hm_server_poll", "hm_server_release",
+    "hm_server_stats", "hm_server_destroy",
 ]
 
 
@@ -99,6 +101,15 @@ _SIGS = {
     "hm_count_matches_static": (_st, [_vp, _vp, ctypes.c_int, _pu64, _vp]),
     "hm_set_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
     "hm_count_batch": (_st, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "hm_server_create": (_st, [_vp, _i32, _i32, _u64, _pvp]),
+    "hm_server_submit": (_st, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _i32, _pu64]),
+    "hm_server_poll": (_st, [_vp, _u64, _i32, ctypes.POINTER(_i32), _pu64, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(_i32), ctypes.POINTER(ctypes.POINTER(_i32)), _pu64]),
+    "hm_server_release": (_st, [_vp, _u64]),
+    "hm_server_stats": (_st, [_vp, _pu64, _pu64, _pu64, _pu64]),
+    "hm_server_destroy": (None, [_vp]),
+    "hm_autotune": (_st, [_vp, _vp, _vp, _i32, ctypes.c_uint32, ctypes.POINTER(hm_tuning),
+                          ctypes.POINTER(ctypes.c_float), _vp]),
     "hm_enumerate_batch": (_st, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "hm_get_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
 }

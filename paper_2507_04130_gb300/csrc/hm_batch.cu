@@ -419,3 +419,63 @@ extern "C" hm_status hm_enumerate_batch(const hm_graph *g, const hm_pattern *con
   if (npat > 0 && (!rows_dev || !row_offsets)) return HM_ERR_ARG;
   return hm::run_batch(g, patterns, modes, npat, rows_dev, row_offsets, counts, (cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------
+// hm_autotune: pick the extension kernel's launch knobs for a workload by
+// timing candidate settings on its batched count.
+// ---------------------------------------------------------------------------
+#include <chrono>
+
+extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *patterns,
+                                 const int32_t *modes, int32_t npat, uint32_t budget_ms,
+                                 hm_tuning *best, float *best_ms, void *stream) {
+  if (!g || !best || npat <= 0 || !patterns || !modes) return HM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  hm_tuning before{};
+  hm_get_tuning(&before);
+  std::vector<uint64_t> counts(npat), ref(npat);
+  // reference run with the current knobs (also warms caches and the pool)
+  hm_status st = hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, ref.data(), s);
+  if (st != HM_OK) return st;
+  static const int32_t kMb[] = {5, 6};
+  static const int32_t kSplit[] = {64, 512};
+  static const int32_t kPair[] = {0, 1};
+  static const int32_t kPoll[] = {32, 128, 512};
+  static const int32_t kFetch[] = {1, 2};
+  std::vector<hm_tuning> cands;
+  cands.push_back(before);
+  for (int32_t mb : kMb)
+    for (int32_t sp : kSplit)
+      for (int32_t pm : kPair)
+        for (int32_t po : kPoll)
+          for (int32_t fe : kFetch) cands.push_back(hm_tuning{mb, sp, pm, fe, po});
+  const auto t_start = std::chrono::steady_clock::now();
+  double best_t = 1e30;
+  hm_tuning pick = before;
+  for (const hm_tuning &c : cands) {
+    if (hm_set_tuning(&c) != HM_OK) continue;
+    double t_min = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+      const auto t0 = std::chrono::steady_clock::now();
+      st = hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, counts.data(), s);
+      const auto t1 = std::chrono::steady_clock::now();
+      if (st != HM_OK) break;
+      t_min = std::min(t_min, std::chrono::duration<double, std::milli>(t1 - t0).count());
+    }
+    if (st != HM_OK || counts != ref) {  // a knob never changes results; treat a mismatch as failure
+      hm_set_tuning(&before);
+      return st != HM_OK ? st : HM_ERR_CUDA;
+    }
+    if (t_min < best_t) {
+      best_t = t_min;
+      pick = c;
+    }
+    const double spent = std::chrono::duration<double, std::milli>(
+                             std::chrono::steady_clock::now() - t_start).count();
+    if (budget_ms && spent > (double)budget_ms) break;
+  }
+  hm_set_tuning(&pick);
+  *best = pick;
+  if (best_ms) *best_ms = (float)best_t;
+  return HM_OK;
+}

@@ -35,6 +35,7 @@
 #include <cuda/atomic>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -1087,10 +1088,11 @@ ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0) {
 // Resident blocks of an extension kernel variant for a dynamic shared-memory size.
 template <bool B = false>
 int extend_grid(bool rows, bool counters, size_t smem, int slot = 0) {
-  static int cache[3][4][64] = {};
+  static std::atomic<int> cache[3][4][64];  // zero-initialised (static storage)
   const int sm = (int)std::min<size_t>(smem / 1024, 63);
-  int &c = cache[slot][(rows ? 2 : 0) + (counters ? 1 : 0)][sm];
-  if (!c) {
+  std::atomic<int> &c = cache[slot][(rows ? 2 : 0) + (counters ? 1 : 0)][sm];
+  int v = c.load(std::memory_order_relaxed);
+  if (!v) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, extend_kernel<B>(rows, counters, slot), kExtThreads, smem);
@@ -1098,9 +1100,10 @@ int extend_grid(bool rows, bool counters, size_t smem, int slot = 0) {
       (void)cudaGetLastError();
       return 0;
     }
-    c = std::max(per_sm, 1) * num_sms();
+    v = std::max(per_sm, 1) * num_sms();
+    c.store(v, std::memory_order_relaxed);
   }
-  return c;
+  return v;
 }
 
 }  // namespace

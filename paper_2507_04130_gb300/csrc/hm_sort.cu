@@ -18,6 +18,7 @@
 //              their per-digit counts, so equal digits keep input order
 //              (stability), and rows are copied to their final slots.
 #include <algorithm>
+#include <atomic>
 
 #include "hm_internal.cuh"
 
@@ -292,15 +293,16 @@ int bits_for(int64_t n) {
 }
 
 int num_sms() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, v = 0;
+  static std::atomic<int> cached{0};
+  int v = cached.load(std::memory_order_relaxed);
+  if (!v) {
+    int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
       v = 1;
-    cached = v;
+    cached.store(v, std::memory_order_relaxed);
   }
-  return cached;
+  return v;
 }
 
 hm_status radix_sort_rows(int32_t *rows, int32_t *tmp, int64_t nrows, int width,

@@ -105,3 +105,18 @@ def test_batch_capacity_and_empty(hm):
                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == hm.binding.HM_ERR_CAPACITY
     assert got.tolist() == counts
+
+
+def test_autotune_picks_valid_knobs_and_keeps_results(hm):
+    g = synth.config2_graph(scale=12)
+    G = hm.Graph.from_synth(g)
+    pats = synth.config4_patterns(count=32)
+    P = [hm.Pattern.from_synth(p) for p in pats]
+    ref = hm.count_batch(G, P, hm.INDUCED)
+    try:
+        best = hm.autotune(G, P, hm.INDUCED, budget_ms=3000)
+        assert best["extend_min_blocks"] in (5, 6, 8) and best["ms"] > 0
+        assert hm.get_tuning() == {k: v for k, v in best.items() if k != "ms"}
+        assert hm.count_batch(G, P, hm.INDUCED) == ref
+    finally:
+        hm.set_tuning()
