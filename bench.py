@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-vs-sequential and serving measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     return ap.parse_args(argv)
@@ -353,6 +355,11 @@ def run_gpu(args):
            "h2d_bytes_per_step": bi // args.steps, "d2h_bytes_per_step": bo // args.steps,
            "path": "hm.Pattern from host arrays + hm_enumerate_matches_part + D2H to pinned host"}
 
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        batched = measure_batched(hm, G, torch)
+        served = measure_serving(hm, G)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         m_cpu, t_cpu, roots, threads, _ = oracle_sample(g, spats, 1, args.cpu_seconds)
@@ -382,10 +389,106 @@ def run_gpu(args):
             "step_ms": [round(x, 3) for x in step_ms],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clock,
+            "batched": batched, "serving": served,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched vs single-query, and served Poisson arrivals (extra keys of the line)
+# ---------------------------------------------------------------------------
+
+def measure_batched(hm, G, torch, reps=3):
+    """256 random induced patterns: one batched pass vs 256 sequential single-pattern calls."""
+    import synth
+
+    pats = synth.config4_patterns()
+    P = [hm.Pattern.from_synth(p) for p in pats]
+    stream = torch.cuda.current_stream()
+    counts = hm.count_batch(G, P, hm.INDUCED)
+    total = sum(counts)
+    tuned = hm.autotune(G, P, hm.INDUCED, budget_ms=4000)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def batched():
+        hm.enumerate_batch(G, P, hm.INDUCED, counts=counts)
+
+    def sequential():
+        for p, c in zip(P, counts):
+            hm.enumerate_matches(G, p, hm.INDUCED, capacity=max(c, 1))
+
+    batched(); sequential()
+    tb = min(timed(batched) for _ in range(reps))
+    ts = min(timed(sequential) for _ in range(reps))
+    hm.set_tuning()
+    return {
+        "workload": ("256 patterns, k ~ U{3..6}, density U[0.4,1.0], vertex labels U{0..7}, arc labels "
+                     "U{0..3}, seed 2, induced, count + sorted rows, on the same R-MAT graph"),
+        "matches": int(total), "patterns_with_matches": int(sum(c > 0 for c in counts)),
+        "batched_ms": round(tb, 3), "sequential_ms": round(ts, 3), "speedup": round(ts / tb, 2),
+        "batched_matches_per_s": round(total / (tb / 1e3), 1),
+        "sequential_matches_per_s": round(total / (ts / 1e3), 1),
+        "autotuned_knobs": tuned,
+    }
+
+
+def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=3.0, max_queries=200,
+                    slots=4, max_batch=32):
+    """Open-loop Poisson arrivals of motif queries against the resident graph, through hm_server."""
+    import threading
+
+    import synth
+
+    out = []
+    for rate in rates:
+        n = int(min(max_queries, max(20, rate * seconds)))
+        arrivals = synth.config5_arrivals(rate, n, n_vlab=8, n_elab=4)
+        srv = hm.Server(G, slots=slots, max_batch=max_batch)
+        ids = [None] * n
+        t0 = time.perf_counter()
+
+        def producer():
+            for i, (t, p, mode) in enumerate(arrivals):
+                delay = t - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids[i] = srv.submit(p, mode, want_rows=True)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        lat, matches = [], 0
+        for i in range(n):
+            while ids[i] is None:
+                time.sleep(0.0002)
+            r = srv.result(ids[i])
+            lat.append(r["latency_ms"])
+            matches += r["count"]
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat.sort()
+        out.append({
+            "rate_qps": rate, "queries": n, "p50_ms": round(statistics.median(lat), 3),
+            "p99_ms": round(lat[min(n - 1, int(round(0.99 * (n - 1))))], 3),
+            "matches": int(matches), "matches_per_s": round(matches / wall, 1),
+            "achieved_qps": round(n / wall, 1), "batches": st["batches"],
+            "max_inflight_batches": st["max_inflight_batches"], "rows_dropped": st["rows_dropped"],
+        })
+    return {"workload": ("Poisson arrivals, k ~ U{3..7}, density U[0.4,1.0], labels uniform over the "
+                         "graph's label sets, mode Bernoulli(1/2), rows returned, resident R-MAT graph; "
+                         f"{slots} dispatcher slots, batches of up to {max_batch}"),
+            "rates": out}
 
 
 # ---------------------------------------------------------------------------
