@@ -287,7 +287,7 @@ hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mod
  *   contents (the call clears what must start at zero): calls whose work
  *   overlaps on the GPU, e.g. on two streams, race on it -- serialise them.
  *   Otherwise as hm_count_matches (same result, same errors). */
-enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3768272 };
+enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3768064 };
 
 hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mode mode,
                                   uint64_t *count, void *stream);
@@ -321,6 +321,11 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      every poll_every candidate chunks (a power of two,
  *                      1..65536, default 128); each request is claimed by
  *                      exactly one busy warp.
+ *   leaf_flatten       1 (default): at the last inner depth, the survivors of
+ *                      a chunk look up their leaf ranges side by side and the
+ *                      ranges are swept together in full 32-lane chunks
+ *                      (survivors with more than 2048 leaf candidates take the
+ *                      ordinary path); -1: one survivor at a time.
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -329,6 +334,7 @@ typedef struct {
   int32_t pair_mode;
   int32_t seeds_per_fetch;
   int32_t poll_every;
+  int32_t leaf_flatten;
 } hm_tuning;
 
 hm_status hm_set_tuning(const hm_tuning *t);
@@ -336,8 +342,9 @@ hm_status hm_get_tuning(hm_tuning *t);
 
 /* hm_autotune -- picks the knobs above for a workload: it times the batched
  * count (hm_count_batch) of the given patterns under candidate settings
- * (blocks per SM 5/6, split threshold 64/512, pair mode 0/1, poll interval
- * 32/128/512, seeds per fetch 1/2, and the current setting), best of two runs
+ * (leaf flattening on/off, blocks per SM 5/6, split threshold 64/512, pair
+ * mode 0/1, poll interval 32/128/512, seeds per fetch 1/2, and the current
+ * setting), best of two runs
  * each, until budget_ms of wall time is spent (0 = try all), installs the
  * fastest with hm_set_tuning and returns it in *best (and its time in
  * *best_ms, may be NULL).  Every run's counts are compared with the first
@@ -372,6 +379,8 @@ typedef struct {
   uint64_t bytes_overlap;
   uint64_t bytes_extend;
   uint64_t candidates;      /* candidate vertices examined by the extension */
+  uint64_t level_chunks[HM_MAX_K];     /* 32-candidate chunks per depth (counters only) */
+  uint64_t level_candidates[HM_MAX_K]; /* candidates per depth (counters only)          */
 } hm_stats;
 
 hm_status hm_last_stats(hm_stats *out);

@@ -15,7 +15,7 @@ HM_OK, HM_ERR_ARG, HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_PATTERN = 0, 1, 2, 
 HM_ERR_OOM, HM_ERR_CAPACITY, HM_ERR_BUDGET, HM_ERR_CUDA, HM_ERR_NO_DEVICE = 5, 6, 7, 8, 9
 HM_MONO, HM_INDUCED = 0, 1
 HM_MAX_K = 16
-HM_STATIC_MAX_ARCS = 3768272
+HM_STATIC_MAX_ARCS = 3768064
 
 #: every function include/hipermotif.h declares
 EXPORTED = [
@@ -50,10 +50,17 @@ class hm_stats(ctypes.Structure):
         ("bytes_overlap", ctypes.c_uint64),
         ("bytes_extend", ctypes.c_uint64),
         ("candidates", ctypes.c_uint64),
+        ("level_chunks", ctypes.c_uint64 * HM_MAX_K),
+        ("level_candidates", ctypes.c_uint64 * HM_MAX_K),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if name.startswith("level_") else v
+        return out
+
 
 
 class hm_tuning(ctypes.Structure):
@@ -63,6 +70,7 @@ class hm_tuning(ctypes.Structure):
         ("pair_mode", ctypes.c_int32),
         ("seeds_per_fetch", ctypes.c_int32),
         ("poll_every", ctypes.c_int32),
+        ("leaf_flatten", ctypes.c_int32),
     ]
 
     def as_dict(self):

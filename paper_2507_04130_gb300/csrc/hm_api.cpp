@@ -11,6 +11,7 @@ std::atomic<int> g_timing{0};
 std::atomic<int> g_counters{0};
 std::atomic<int> g_min_blocks{5}, g_split_min{64}, g_pair_mode{0}, g_seeds_per_fetch{1};
 std::atomic<int> g_poll_every{128};
+std::atomic<int> g_leaf_flatten{1};
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -26,6 +27,7 @@ hm_tuning tuning() {
   t.pair_mode = g_pair_mode.load(std::memory_order_relaxed);
   t.seeds_per_fetch = g_seeds_per_fetch.load(std::memory_order_relaxed);
   t.poll_every = g_poll_every.load(std::memory_order_relaxed);
+  t.leaf_flatten = g_leaf_flatten.load(std::memory_order_relaxed);
   return t;
 }
 uint64_t budget_ms() { return g_budget_ms.load(std::memory_order_relaxed); }
@@ -77,13 +79,15 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   const int sp = t->seeds_per_fetch ? t->seeds_per_fetch : 1;
   const int pe = t->poll_every ? t->poll_every : 128;
   if ((mb != 5 && mb != 6 && mb != 8) || sm < 2 || sp < 1 || sp > 1024 ||
-      (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)))
+      (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)) ||
+      t->leaf_flatten < -1 || t->leaf_flatten > 1)
     return HM_ERR_ARG;
   hm::g_min_blocks.store(mb);
   hm::g_split_min.store(sm);
   hm::g_pair_mode.store(t->pair_mode);
   hm::g_seeds_per_fetch.store(sp);
   hm::g_poll_every.store(pe);
+  hm::g_leaf_flatten.store(t->leaf_flatten < 0 ? -1 : 1);
   return HM_OK;
 }
 

@@ -311,6 +311,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   A.pair_mode = tu.pair_mode;
   A.seeds_per_fetch = tu.seeds_per_fetch;
   A.poll_mask = (uint32_t)tu.poll_every - 1u;
+    A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
   A.seeds = seeds;
   A.nseeds = nseeds;
   A.qbuf = qbuf;
@@ -442,13 +443,15 @@ extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *pat
   static const int32_t kPair[] = {0, 1};
   static const int32_t kPoll[] = {32, 128, 512};
   static const int32_t kFetch[] = {1, 2};
+  static const int32_t kFlat[] = {1, -1};
   std::vector<hm_tuning> cands;
   cands.push_back(before);
-  for (int32_t mb : kMb)
-    for (int32_t sp : kSplit)
-      for (int32_t pm : kPair)
-        for (int32_t po : kPoll)
-          for (int32_t fe : kFetch) cands.push_back(hm_tuning{mb, sp, pm, fe, po});
+  for (int32_t fl : kFlat)
+    for (int32_t mb : kMb)
+      for (int32_t sp : kSplit)
+        for (int32_t pm : kPair)
+          for (int32_t po : kPoll)
+            for (int32_t fe : kFetch) cands.push_back(hm_tuning{mb, sp, pm, fe, po, fl});
   const auto t_start = std::chrono::steady_clock::now();
   double best_t = 1e30;
   hm_tuning pick = before;

@@ -2,7 +2,6 @@
 // (hm_match.cu) and batched (hm_batch.cu) entry points.  Each translation unit
 // that includes it gets its own copy of these kernels.
 //
-//
 //   k_edge_seed     every target arc is tried as the image of the reordered
 //                   pattern arc between positions 0 and 1 (the loop "for all
 //                   e in E2" of the HiPerMotif algorithm): vertex validator
@@ -21,10 +20,12 @@
 //                   checks one candidate (injectivity, label, degrees, the
 //                   other arcs by binary search, induced non-arcs) and a
 //                   ballot gives the survivors.  The depth-first stack lives in
-//                   shared memory.  Idle warps advertise themselves; busy warps
-//                   split the shallowest unfinished range and donate half
-//                   through a bounded lock-free queue.  Every wait is bounded
-//                   by the call's time budget.
+//                   shared memory.  At the last inner depth the survivors'
+//                   leaf ranges are swept together (leaf_flatten).  Idle warps
+//                   post donation requests; a busy warp claims one and splits
+//                   off half of its shallowest unfinished range through a
+//                   bounded lock-free queue.  Every wait is bounded by the
+//                   call's time budget.
 //   k_seed_rows     two-vertex patterns: each seed is already a match.
 //
 // Output: a match count (uint64), and optionally rows in original pattern
@@ -92,6 +93,8 @@ struct Ctl {
   unsigned long long bytes_overlap;
   unsigned long long bytes_extend;
   unsigned long long lanes;                   // candidates examined (instrumented launches only)
+  unsigned long long level_chunks[kMaxK];     // per depth (instrumented launches only)
+  unsigned long long level_lanes[kMaxK];
 };
 
 struct ExtArgs {
@@ -99,6 +102,8 @@ struct ExtArgs {
   int32_t pair_mode;        // spread (candidate, condition) pairs over lanes on short ranges
   int32_t seeds_per_fetch;  // seeds a warp claims at once
   uint32_t poll_mask;       // a busy warp looks for donation requests every poll_mask+1 chunks
+  int32_t leaf_flatten;     // run the last depth of all survivors of a chunk together
+  int32_t pad3;
   const int2 *seeds;
   const unsigned long long *nseeds;
   Task *qbuf;
@@ -545,6 +550,214 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
   return search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) < 0;
 }
 
+// ---- last-level flattening ---------------------------------------------------
+//
+// At the last inner depth L = k-2, the survivors of a chunk (up to 32, one per
+// lane) are not descended into one by one.  Each survivor lane looks up its
+// own label groups and picks its own shortest anchor range for the leaf; the
+// ranges are concatenated (warp prefix sum) and swept in full 32-lane chunks,
+// each lane finding its survivor by a binary search over the prefix sums.
+// Survivors whose leaf range exceeds kFlatMax stay pending for the ordinary
+// descent, where their range can be split and donated.
+constexpr int32_t kFlatMax = 2048;
+
+// The survivor (image of depth L) a flattened leaf candidate belongs to.
+struct LeafOwner {
+  int32_t c, off_out, off_in, deg_out, deg_in;
+  int2 own[2];  // label group of the leaf inside c's out-list [0] / in-list [1]
+};
+
+template <bool kC>
+__device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, const WarpState &S,
+                                           const int2 *__restrict__ grp, int p, int drive, int32_t d,
+                                           const LeafOwner &o, const uint8_t *root_mask,
+                                           uint64_t &ctr) {
+  const int L = p - 1;
+  if (d == o.c) return false;
+  for (int i = 0; i < L; ++i)
+    if (S.map[i] == d) return false;                        // injective
+  if (root_mask && p == P.root_pos && !root_mask[d]) return false;
+  const int nc = P.ncons[p];
+  if (nc <= 1) return true;
+  if (kC) ctr += 32;
+  const int4 vi = __ldg(&G.vi[d]);
+  const int2 od = __ldg(&G.off[d]);
+  for (int j = 0; j < nc; ++j) {
+    if (j == drive) continue;
+    const Cons cs = P.cons[p][j];
+    const int q = cs.q;
+    const bool mine = q == L;
+    const int32_t fq = mine ? o.c : S.map[q];
+    const int32_t q_off_out = mine ? o.off_out : S.off_out[q];
+    const int32_t q_off_in = mine ? o.off_in : S.off_in[q];
+    const bool fwd = cs.kind == kOut || cs.kind == kNotOut;   // arc f(q) -> d ?
+    if (cs.kind <= kIn) {
+      const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
+      const int32_t rev_len = fwd ? vi.z : vi.y;
+      if (r.y == 0 || rev_len == 0) return false;
+      bool found;
+      if (rev_len < r.y) {
+        const int32_t i = fwd ? search_c<kC>(G.in_adj, od.y, rev_len, fq, ctr)
+                              : search_c<kC>(G.out_adj, od.x, rev_len, fq, ctr);
+        if (kC && i >= 0) ctr += 4;
+        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+      } else {
+        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, (fwd ? q_off_out : q_off_in) + r.x, r.y,
+                             d, ctr) >= 0;
+      }
+      if (!found) return false;
+    } else {
+      const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[q]) : (mine ? o.deg_in : S.deg_in[q]);
+      const int32_t lb = fwd ? vi.z : vi.y;
+      if (la == 0 || lb == 0) continue;
+      const bool found =
+          la <= lb ? search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? q_off_out : q_off_in, la, d, ctr) >= 0
+                   : search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? od.y : od.x, lb, fq, ctr) >= 0;
+      if (found) return false;
+    }
+  }
+  return true;
+}
+
+// Runs the leaf of every survivor in `m` (bits over adj[base + lane]) that has
+// at most kFlatMax leaf candidates; returns the survivors left for the
+// ordinary descent.  Adds the matches to task_count and writes their rows.
+template <bool kRows, bool kC>
+__device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpState &S,
+                                 int2 *__restrict__ grp, int L, const int32_t *__restrict__ adj,
+                                 int32_t base, uint32_t m, int lane, const uint8_t *root_mask,
+                                 unsigned long long &task_count, unsigned long long *row_cursor,
+                                 int32_t *row_base, unsigned long long row_cap, Ctl *ctl,
+                                 unsigned long long &chunks, uint64_t &ctr) {
+  const int p = L + 1;
+  const int k = P.k;
+  const int npos = P.npos[p];
+  // label groups of anchors mapped before depth L are the same for every survivor
+  for (int j = 0; j < npos; ++j) {
+    const Cons cs = P.cons[p][j];
+    if (cs.q == L) continue;
+    const int4 dq = S.dir[cs.q];
+    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G.gdir_out, dq.x, dq.y, cs.lab, P.vlab[p], lane, ctr)
+                                   : dir_lookup<kC>(G.gdir_in, dq.z, dq.w, cs.lab, P.vlab[p], lane, ctr);
+    if (lane == 0) grp[P.gbase[p] + j] = r;
+  }
+  __syncwarp();
+  // each survivor lane: its record, its own label groups, its shortest range
+  const bool mine = (m >> lane) & 1u;
+  LeafOwner o{};
+  int32_t drv_j = 0, drv_lo = 0, drv_len = 0, drv_kind = 0;
+  if (mine) {
+    const int32_t c = __ldg(adj + base + lane);
+    const int4 vi = __ldg(&G.vi[c]);
+    const int2 of = __ldg(&G.off[c]);
+    const int4 vd = __ldg(&G.vdir[c]);
+    if (kC) ctr += 52;
+    o.c = c;
+    o.off_out = of.x;
+    o.off_in = of.y;
+    o.deg_out = vi.y;
+    o.deg_in = vi.z;
+    int32_t best = INT32_MAX;
+    for (int j = 0; j < npos; ++j) {
+      const Cons cs = P.cons[p][j];
+      int2 r;
+      int32_t lo;
+      if (cs.q == L) {
+        const int4 *dir = cs.kind == kOut ? G.gdir_out : G.gdir_in;
+        const int32_t first = cs.kind == kOut ? vd.x : vd.z, cnt = cs.kind == kOut ? vd.y : vd.w;
+        r = make_int2(0, 0);
+        for (int32_t e = 0; e < cnt; ++e) {
+          const int4 ent = __ldg(dir + first + e);
+          if (kC) ctr += 16;
+          if (ent.x == cs.lab && ent.y == P.vlab[p]) {
+            r = make_int2(ent.z, ent.w - ent.z);
+            break;
+          }
+        }
+        o.own[cs.kind] = r;
+        lo = (cs.kind == kOut ? of.x : of.y) + r.x;
+      } else {
+        r = grp[P.gbase[p] + j];
+        lo = (cs.kind == kOut ? S.off_out[cs.q] : S.off_in[cs.q]) + r.x;
+      }
+      if (r.y < best) {
+        best = r.y;
+        drv_j = j;
+        drv_lo = lo;
+        drv_kind = cs.kind;
+      }
+    }
+    drv_len = best;
+  }
+  const uint32_t keep = __ballot_sync(kFull, mine && drv_len > kFlatMax);
+  const int32_t len = (mine && drv_len <= kFlatMax) ? drv_len : 0;
+  int32_t incl = len;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int32_t y = __shfl_up_sync(kFull, incl, off);
+    if (lane >= off) incl += y;
+  }
+  const int32_t excl = incl - len;
+  const int32_t total = __shfl_sync(kFull, incl, 31);
+  if (kC && lane == 0 && total) {
+    atomicAdd(&ctl->level_chunks[p], (unsigned long long)((total + 31) / 32));
+    atomicAdd(&ctl->level_lanes[p], (unsigned long long)total);
+  }
+  chunks += (unsigned long long)((total + 31) / 32);
+  for (int32_t chunk = 0; chunk < total; chunk += 32) {
+    const int32_t g = chunk + lane;
+    // owner: the first survivor lane whose inclusive prefix exceeds g
+    int32_t lo_l = 0, hi_l = 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+      const int32_t mid = (lo_l + hi_l) >> 1;
+      const int32_t v = __shfl_sync(kFull, incl, mid);
+      if (g < v) hi_l = mid; else lo_l = mid + 1;
+    }
+    const int ow = min(lo_l, 31);
+    LeafOwner oo;
+    oo.c = __shfl_sync(kFull, o.c, ow);
+    oo.off_out = __shfl_sync(kFull, o.off_out, ow);
+    oo.off_in = __shfl_sync(kFull, o.off_in, ow);
+    oo.deg_out = __shfl_sync(kFull, o.deg_out, ow);
+    oo.deg_in = __shfl_sync(kFull, o.deg_in, ow);
+    oo.own[0].x = __shfl_sync(kFull, o.own[0].x, ow);
+    oo.own[0].y = __shfl_sync(kFull, o.own[0].y, ow);
+    oo.own[1].x = __shfl_sync(kFull, o.own[1].x, ow);
+    oo.own[1].y = __shfl_sync(kFull, o.own[1].y, ow);
+    const int32_t o_drv_j = __shfl_sync(kFull, drv_j, ow);
+    const int32_t o_drv_lo = __shfl_sync(kFull, drv_lo, ow);
+    const int32_t o_drv_kind = __shfl_sync(kFull, drv_kind, ow);
+    const int32_t o_excl = __shfl_sync(kFull, excl, ow);
+    bool ok = false;
+    int32_t d = -1;
+    if (g < total) {
+      d = __ldg((o_drv_kind == kOut ? G.gout_adj : G.gin_adj) + o_drv_lo + (g - o_excl));
+      if (kC) ctr += 4;
+      ok = check_leaf<kC>(G, P, S, grp, p, o_drv_j, d, oo, root_mask, ctr);
+    }
+    const uint32_t bal = __ballot_sync(kFull, ok);
+    const int nm = __popc(bal);
+    task_count += nm;
+    if (kRows && nm) {
+      unsigned long long at = 0;
+      if (lane == 0) at = atomicAdd(row_cursor, (unsigned long long)nm);
+      at = __shfl_sync(kFull, at, 0);
+      if (ok) {
+        const unsigned long long r = at + __popc(bal & lanemask_lt());
+        if (r < row_cap) {
+          if (kC) ctr += 4 * k;
+          int32_t *row = row_base + r * k;
+          for (int i = 0; i < L; ++i) row[P.orig[i]] = S.map[i];
+          row[P.orig[L]] = oo.c;
+          row[P.orig[p]] = d;
+        }
+      }
+    }
+  }
+  return keep;
+}
+
 // ---- bounded lock-free queue (Vyukov-style sequence numbers) --------------
 
 __device__ bool q_push(const ExtArgs &A, WarpState &S, int lane) {
@@ -695,6 +908,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
   const unsigned long long deadline = globaltimer_ns() + A.budget_ns;
   const unsigned long long nseeds = *A.nseeds;
   unsigned long long my_count = 0, my_chunks = 0;
+  unsigned long long chunks_flushed = 0, next_check = 64, next_poll = A.poll_mask + 1ull;
   unsigned long long seed_at = 0, seed_end = 0;  // this warp's claimed seeds
   int32_t requests_seen = 0, status_seen = kStatOk;  // lane 0: values from the previous poll
   bool seeds_done = false, stop = false;
@@ -828,11 +1042,14 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           continue;
         }
         ++my_chunks;
-        if ((my_chunks & 63) == 0) {
-          // budget check; the status word read here was requested 64 chunks
-          // ago, so its latency is hidden behind that work
+        if (my_chunks >= next_check) {
+          // budget check every 64 chunks; the status word read here was
+          // requested at the previous check, so its latency is hidden
+          next_check = my_chunks + 64;
           int halt = 0;
           if (lane == 0) {
+            const unsigned long long add = my_chunks - chunks_flushed;
+            chunks_flushed = my_chunks;
             const int32_t status = status_seen;
             status_seen = ld_volatile(&A.ctl->status);
             if (status != kStatOk) halt = 1;
@@ -840,18 +1057,19 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
               atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
               halt = 1;
             } else if (A.max_chunks) {
-              unsigned long long tot = atomicAdd(&A.ctl->chunks, 64ull) + 64;
+              unsigned long long tot = atomicAdd(&A.ctl->chunks, add) + add;
               if (tot > A.max_chunks) {
                 atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
                 halt = 1;
               }
             } else {
-              atomicAdd(&A.ctl->chunks, 64ull);
+              atomicAdd(&A.ctl->chunks, add);
             }
           }
           if (__shfl_sync(kFull, halt, 0)) { stop = true; break; }
         }
-        if ((my_chunks & A.poll_mask) == 0) {
+        if (my_chunks >= next_poll) {
+          next_poll = my_chunks + A.poll_mask + 1ull;
           // donate only while fewer tasks wait in the queue than warps wait
           // for work; the idle-warp count used is the one requested at the
           // previous poll, so the poll does not stall the warp
@@ -922,6 +1140,10 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           m = __ballot_sync(kFull, ok);
         }
         if (lane == 0) S.lo[level] = lo + take;
+        if (kC && lane == 0) {
+          atomicAdd(&A.ctl->level_chunks[level], 1ull);
+          atomicAdd(&A.ctl->level_lanes[level], (unsigned long long)min((int32_t)take, hi - lo));
+        }
         if (leaf) {
           // leaf: every survivor is a match
           const int nm = __popc(m);
@@ -943,8 +1165,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           __syncwarp();
           continue;
         }
+        uint32_t pending = m;
+        if (A.leaf_flatten && level == k - 2 && m)
+          pending = leaf_flatten<kRows, kC>(G, P, S, grp, level, adj, lo, m, lane, A.root_mask,
+                                            task_count, row_cursor, row_base, row_cap, A.ctl,
+                                            my_chunks, ctr);
         if (lane == 0) {
-          S.mask[level] = m;
+          S.mask[level] = pending;
           S.base[level] = lo;
         }
         __syncwarp();
@@ -974,7 +1201,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
   if (lane == 0) {
     if (!stop) atomicSub(&A.ctl->active, 1);
     if (my_count) atomicAdd(&A.ctl->count, my_count);
-    if (my_chunks & 63) atomicAdd(&A.ctl->chunks, my_chunks & 63);
+    if (my_chunks > chunks_flushed) atomicAdd(&A.ctl->chunks, my_chunks - chunks_flushed);
   }
   if (kC) {
     for (int o = 16; o; o >>= 1) {

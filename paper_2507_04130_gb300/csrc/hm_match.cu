@@ -128,6 +128,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.pair_mode = tu.pair_mode;
     A.seeds_per_fetch = tu.seeds_per_fetch;
     A.poll_mask = (uint32_t)tu.poll_every - 1u;
+    A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
     const int grid = extend_grid(rows, counters, smem, slot);
@@ -154,6 +155,10 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   st.bytes_overlap = h.bytes_overlap;
   st.bytes_extend = h.bytes_extend;
   st.candidates = h.lanes;
+  for (int i = 0; i < kMaxK; ++i) {
+    st.level_chunks[i] = h.level_chunks[i];
+    st.level_candidates[i] = h.level_lanes[i];
+  }
   st.kernel_launches = launches;
   if (h.status == kStatBudget) return HM_ERR_BUDGET;
   if (h.status != kStatOk) return HM_ERR_CUDA;
@@ -242,7 +247,8 @@ namespace hm {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
-constexpr size_t kStaticCtlBytes = (sizeof(Ctl) + 255) / 256 * 256;
+constexpr size_t kStaticCtlBytes = 4096;  // fixed room for the control block
+static_assert(sizeof(Ctl) <= kStaticCtlBytes, "control block outgrew its static room");
 constexpr size_t kStaticQseqBytes = sizeof(unsigned long long) * kQueueCap;
 constexpr size_t kStaticQbufBytes = sizeof(Task) * kQueueCap;
 constexpr size_t kStaticSeedBase = kStaticCtlBytes + kStaticQseqBytes + kStaticQbufBytes;
@@ -346,6 +352,7 @@ extern "C" hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern
     A.pair_mode = tu.pair_mode;
     A.seeds_per_fetch = tu.seeds_per_fetch;
     A.poll_mask = (uint32_t)tu.poll_every - 1u;
+    A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
     const int grid = extend_grid(false, false, smem, slot);

@@ -250,7 +250,12 @@ def test_unlabelled_hubs_force_donation(hm):
     sp = synth.Pattern(4, np.array([0, 1, 2], np.int32), np.array([1, 2, 3], np.int32),
                        np.zeros(4, np.int32), np.zeros(3, np.int32), "path4")
     _check(hm, G, og, sp, oracle.MONO, rows=False)
-    st = hm.last_stats()
+    hm.set_tuning(leaf_flatten=-1)   # one survivor at a time: every range can be split
+    try:
+        _check(hm, G, og, sp, oracle.MONO, rows=False)
+        st = hm.last_stats()
+    finally:
+        hm.set_tuning()
     assert st["tasks_donated"] > 0
 
 
@@ -383,7 +388,8 @@ def test_instrumented_kernels_agree_and_count_bytes(hm):
 @pytest.mark.parametrize("knobs", [dict(extend_min_blocks=6), dict(extend_min_blocks=8),
                                    dict(pair_mode=1), dict(split_min=2, seeds_per_fetch=7),
                                    dict(pair_mode=1, split_min=2, poll_every=1),
-                                   dict(poll_every=65536),
+                                   dict(poll_every=65536), dict(leaf_flatten=-1),
+                                   dict(leaf_flatten=-1, pair_mode=1, split_min=2),
                                    dict(split_min=1000, seeds_per_fetch=64)])
 def test_tuning_knobs_never_change_results(hm, knobs):
     g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
