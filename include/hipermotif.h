@@ -57,7 +57,7 @@ typedef enum {
 
 typedef enum { HM_MONO = 0, HM_INDUCED = 1 } hm_mode;
 
-enum { HM_MAX_K = 16 };
+enum { HM_MAX_K = 20 };
 
 typedef struct hm_graph hm_graph;     /* opaque: device-resident target graph  */
 typedef struct hm_pattern hm_pattern; /* opaque: reordered pattern and plans   */
@@ -90,6 +90,32 @@ hm_status hm_load_graph(int32_t n, int64_t m, const int32_t *src, const int32_t 
                         void *stream, hm_graph **out);
 
 void hm_free_graph(hm_graph *g);
+
+/* hm_load_graph_props -- hm_load_graph with several int32 properties per
+ * vertex and per arc.  checkAttributes of the validators compares every
+ * property (Sec. III-B; arbitrary numbers of properties, Sec. III-D): two
+ * vertices (arcs) have equal labels exactly when all their properties are
+ * equal.  Each distinct property tuple is given its rank in the sorted list of
+ * distinct tuples as its label, the graph is built on those labels, and the
+ * sorted tuple tables are kept with the graph (host memory) for
+ * hm_load_pattern_props.
+ *   nvp, nep    properties per vertex / per arc, 1..64.
+ *   vprops      HOST int32[n * nvp], row-major (vertex v's tuple at v * nvp).
+ *   eprops      HOST int32[m * nep], row-major, parallel to src/dst (HOST).
+ * Errors as hm_load_graph. */
+hm_status hm_load_graph_props(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                              int32_t nvp, const int32_t *vprops, int32_t nep,
+                              const int32_t *eprops, void *stream, hm_graph **out);
+
+/* hm_load_pattern_props -- a pattern for a graph loaded with
+ * hm_load_graph_props: its vertices carry g's nvp properties (HOST int32[k *
+ * nvp]) and its arcs g's nep properties (HOST int32[mp * nep]).  A tuple g
+ * does not have gets label -1, which no target vertex or arc carries.
+ * Otherwise as hm_load_pattern (Alg. 1, validation).  HM_ERR_ARG if g was not
+ * loaded with properties. */
+hm_status hm_load_pattern_props(const hm_graph *g, int32_t k, int32_t mp, const int32_t *src,
+                                const int32_t *dst, const int32_t *vprops,
+                                const int32_t *eprops, hm_pattern **out);
 
 /* Sizes of a loaded graph (host outputs; any may be NULL). */
 hm_status hm_graph_info(const hm_graph *g, int32_t *n, int64_t *m, size_t *device_bytes);
@@ -287,7 +313,7 @@ hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mod
  *   contents (the call clears what must start at zero): calls whose work
  *   overlaps on the GPU, e.g. on two streams, race on it -- serialise them.
  *   Otherwise as hm_count_matches (same result, same errors). */
-enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3768064 };
+enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3702528 };
 
 hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mode mode,
                                   uint64_t *count, void *stream);

@@ -48,7 +48,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OG_MAXK 16
+#define OG_MAXK 24
 
 enum { OG_OK = 0, OG_EARG = -1, OG_ESELF = -2, OG_EDUP = -3, OG_ENOMEM = -4 };
 

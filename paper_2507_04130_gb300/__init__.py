@@ -77,6 +77,23 @@ class Graph:
         self.n, self.m = int(n), m
 
     @classmethod
+    def with_properties(cls, n: int, src, dst, vprops, eprops, stream=None):
+        """A graph whose vertices / arcs carry several int32 properties (arrays [n, nvp], [m, nep])."""
+        vp = np.ascontiguousarray(np.asarray(vprops, dtype=np.int32).reshape(n, -1))
+        keep = [_host_i32(src), _host_i32(dst)]
+        m = int(keep[0].shape[0])
+        ep = np.ascontiguousarray(np.asarray(eprops, dtype=np.int32).reshape(m, -1))
+        h = ctypes.c_void_p()
+        check(lib.hm_load_graph_props(int(n), m, _ptr(keep[0]), _ptr(keep[1]), vp.shape[1], _ptr(vp),
+                                      ep.shape[1], _ptr(ep), _stream_ptr(stream), ctypes.byref(h)),
+              "hm_load_graph_props")
+        self = cls.__new__(cls)
+        self._h = h
+        self.n, self.m = int(n), m
+        self.nvp, self.nep = int(vp.shape[1]), int(ep.shape[1])
+        return self
+
+    @classmethod
     def from_synth(cls, g, stream=None, device: bool = False):
         if device:
             t = [torch.from_numpy(np.asarray(a)).cuda() for a in (g.src, g.dst, g.vlab, g.elab)]
@@ -132,6 +149,21 @@ class Pattern:
     @classmethod
     def from_synth(cls, p):
         return cls(p.k, p.src, p.dst, p.vlab, p.elab)
+
+    @classmethod
+    def with_properties(cls, g: "Graph", k: int, src, dst, vprops, eprops):
+        """A pattern whose vertices / arcs carry g's property tuples ([k, nvp], [mp, nep])."""
+        keep = [_host_i32(src), _host_i32(dst)]
+        mp = int(keep[0].shape[0])
+        vp = np.ascontiguousarray(np.asarray(vprops, dtype=np.int32).reshape(k, -1))
+        ep = np.ascontiguousarray(np.asarray(eprops, dtype=np.int32).reshape(mp, -1))
+        h = ctypes.c_void_p()
+        check(lib.hm_load_pattern_props(g.handle, int(k), mp, _ptr(keep[0]), _ptr(keep[1]), _ptr(vp),
+                                        _ptr(ep), ctypes.byref(h)), "hm_load_pattern_props")
+        self = cls.__new__(cls)
+        self._h = h
+        self.k, self.mp = int(k), mp
+        return self
 
     @property
     def handle(self):

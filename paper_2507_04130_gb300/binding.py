@@ -14,8 +14,8 @@ from . import _build
 HM_OK, HM_ERR_ARG, HM_ERR_SELF_LOOP, HM_ERR_DUP_EDGE, HM_ERR_PATTERN = 0, 1, 2, 3, 4
 HM_ERR_OOM, HM_ERR_CAPACITY, HM_ERR_BUDGET, HM_ERR_CUDA, HM_ERR_NO_DEVICE = 5, 6, 7, 8, 9
 HM_MONO, HM_INDUCED = 0, 1
-HM_MAX_K = 16
-HM_STATIC_MAX_ARCS = 3768064
+HM_MAX_K = 20
+HM_STATIC_MAX_ARCS = 3702528
 
 #: every function include/hipermotif.h declares
 EXPORTED = [
@@ -27,7 +27,7 @@ EXPORTED = [
     "hm_last_stats", "hm_set_timing", "hm_set_counters", "hm_count_matches_static",
     "hm_set_tuning", "hm_get_tuning", "hm_count_batch", "hm_enumerate_batch", "hm_autotune",
     "hm_server_create", "hm_server_submit", "hm_server_poll", "hm_server_release",
-    "hm_server_stats", "hm_server_destroy",
+    "hm_server_stats", "hm_server_destroy", "hm_load_graph_props", "hm_load_pattern_props",
 ]
 
 
@@ -94,6 +94,8 @@ _SIGS = {
     "hm_graph_export": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hm_graph_export_groups": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hm_load_pattern": (_st, [_i32, _i32, _vp, _vp, _vp, _vp, _pvp]),
+    "hm_load_graph_props": (_st, [_i32, _i64, _vp, _vp, _i32, _vp, _i32, _vp, _vp, _pvp]),
+    "hm_load_pattern_props": (_st, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _pvp]),
     "hm_free_pattern": (None, [_vp]),
     "hm_pattern_order": (_st, [_vp, _vp]),
     "hm_count_matches": (_st, [_vp, _vp, ctypes.c_int, _pu64, _vp]),

@@ -388,6 +388,8 @@ extern "C" hm_status hm_load_graph(int32_t n, int64_t m, const int32_t *src, con
 extern "C" void hm_free_graph(hm_graph *g) {
   if (!g) return;
   free_graph_arrays(g);
+  free(g->vtab);
+  free(g->etab);
   delete g;
 }
 

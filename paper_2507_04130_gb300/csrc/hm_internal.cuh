@@ -181,6 +181,11 @@ struct hm_graph {
   int4 *gdir_out, *gdir_in, *vdir;
   int64_t ndir_out, ndir_in;
   size_t bytes;
+  // multi-property graphs (hm_load_graph_props): the sorted distinct property
+  // tuples of vertices and arcs (host, malloc'ed); a label is a tuple's rank
+  int32_t nvp, nep;
+  int64_t nvtab, netab;
+  int32_t *vtab, *etab;
   hm::DevGraph dev() const {
     return hm::DevGraph{n,        m,       src,      out_adj,  out_elab, in_adj, in_elab, vi,
                         off,      gout_adj, gin_adj, gdir_out, gdir_in,  vdir};

@@ -70,7 +70,7 @@ struct Task {
   int32_t pad[2];
   int32_t map[kMaxK];
 };
-static_assert(sizeof(Task) == 96, "task layout");
+static_assert(sizeof(Task) == 32 + 4 * kMaxK && sizeof(Task) % 16 == 0, "task layout");
 constexpr int kTaskWords = sizeof(Task) / 4;
 
 // Control block of one call.  Words that different warps hit at high rates
@@ -1102,7 +1102,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         int32_t c = -1;
         uint32_t m;
         int take;
-        if (A.pair_mode && J >= 2 && (hi - lo) * J <= 32) {
+        if (A.pair_mode && J >= 2 && J < 32 && (hi - lo) * J <= 32) {
           // the whole range fits one round of (candidate, condition) pairs:
           // a candidate's searches run side by side instead of one after another
           take = (int)(hi - lo);

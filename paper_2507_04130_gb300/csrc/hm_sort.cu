@@ -30,7 +30,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 4;
 constexpr int kTile = kSortThreads * kItems;
-constexpr int kMaxKeyCols = 17;
+constexpr int kMaxKeyCols = HM_MAX_K + 1;
 
 struct KeySpec {
   int ncols;                 // key columns
@@ -202,6 +202,10 @@ ScatterFn scatter_for(int width) {
     case 15: return launch_scatter<15>;
     case 16: return launch_scatter<16>;
     case 17: return launch_scatter<17>;
+    case 18: return launch_scatter<18>;
+    case 19: return launch_scatter<19>;
+    case 20: return launch_scatter<20>;
+    case 21: return launch_scatter<21>;
     default: return nullptr;
   }
 }

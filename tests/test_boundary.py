@@ -62,7 +62,7 @@ def test_pattern_order_hand_worked(hm, case):
 @pytest.mark.parametrize("seed", range(40))
 def test_pattern_order_equals_plain_alg1(hm, seed):
     rng = np.random.default_rng(seed)
-    k = int(rng.integers(2, 17))
+    k = int(rng.integers(2, 21))
     p = synth.random_pattern(rng, k, float(rng.uniform(0.05, 0.8)), n_vlab=2, n_elab=2)
     assert hm.Pattern.from_synth(p).order == steps.structural_reorder(k, p.src, p.dst)
 
@@ -74,7 +74,7 @@ def test_config_patterns_order(hm):
 
 @pytest.mark.parametrize("k,src,dst,status", [
     (1, [0], [0], "HM_ERR_PATTERN"),                       # k < 2
-    (17, [0], [1], "HM_ERR_PATTERN"),                      # k > 16
+    (21, [0], [1], "HM_ERR_PATTERN"),                      # k > 20
     (3, [], [], "HM_ERR_PATTERN"),                         # no arc
     (3, [0, 1], [0, 2], "HM_ERR_SELF_LOOP"),
     (3, [0, 0], [1, 1], "HM_ERR_DUP_EDGE"),
