@@ -49,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-sequential and serving measurements")
+    ap.add_argument("--ablation", action="store_true",
+                    help="instead: the reordering ablation (Alg. 1 vs breadth-first order) on 60 ER graphs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     return ap.parse_args(argv)
@@ -535,9 +537,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# ablation: Alg. 1's order vs breadth-first order (no reordering)
+# ---------------------------------------------------------------------------
+
+def bfs_order(k, src, dst):
+    """Breadth-first visiting order from vertex 0, neighbours ascending (every position anchored)."""
+    adj = {v: set() for v in range(k)}
+    for a, b in zip(src, dst):
+        adj[int(a)].add(int(b))
+        adj[int(b)].add(int(a))
+    order, seen = [0], {0}
+    for v in order:
+        for w in sorted(adj[v]):
+            if w not in seen:
+                seen.add(w)
+                order.append(w)
+    return order
+
+
+def run_ablation(args):
+    """Reordering ablation on a family of 60 ER graphs (edge probability 0.0005-0.1,
+    1k-1.5M arcs, uniform random labels) with random patterns of 3-20 vertices:
+    the GPU count with Alg. 1's order vs breadth-first order from vertex 0."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2507_04130_gb300 as hm
+
+    torch.cuda.set_device(0)
+    hm.set_timing(True)
+    hm.set_budget(2000, 0)
+    rng = np.random.default_rng(5)
+    cases = []
+    for i in range(60):
+        pr = 10 ** rng.uniform(math.log10(0.0005), math.log10(0.1))
+        m = int(10 ** rng.uniform(3, math.log10(1.5e6)))
+        n = max(int(math.sqrt(m / pr)) + 1, 64)
+        m = min(m, n * (n - 1) // 2)
+        g = synth.er_graph(n, m, 4, 2, seed=100 + i)
+        k = int(rng.integers(3, 21))
+        sp = synth.random_pattern(rng, k, float(rng.uniform(0.1, 0.35)), n_vlab=4, n_elab=2)
+        G = hm.Graph.from_synth(g)
+        res = {}
+        for name, order in (("alg1", None), ("bfs", bfs_order(k, sp.src, sp.dst))):
+            P = hm.Pattern.from_synth(sp, order=order)
+            try:
+                hm.count_matches(G, P, hm.MONO)
+                ms = []
+                for _ in range(3):
+                    c = hm.count_matches(G, P, hm.MONO)
+                    st = hm.last_stats()
+                    ms.append(st["ms_edge_scan"] + st["ms_overlap"] + st["ms_extend"])
+                res[name] = (c, statistics.median(ms))
+            except hm.HMError as e:
+                res[name] = (None, None if e.status == hm.binding.HM_ERR_BUDGET else -1)
+        G.close()
+        case = {"n": n, "m": m, "p": round(pr, 6), "k": k, "arcs": sp.mp}
+        if res["alg1"][0] is not None and res["bfs"][0] is not None:
+            assert res["alg1"][0] == res["bfs"][0]
+            case.update(count=res["alg1"][0], alg1_ms=round(res["alg1"][1], 4),
+                        bfs_ms=round(res["bfs"][1], 4), speedup=round(res["bfs"][1] / res["alg1"][1], 3))
+        else:
+            case.update(skipped="time budget (2 s) exceeded by " +
+                        ",".join(nm for nm, r in res.items() if r[0] is None))
+        cases.append(case)
+    sp_ = [c["speedup"] for c in cases if "speedup" in c]
+    # below ~0.2 ms both orders are launch-latency bound and the ratio is noise
+    big = [c["speedup"] for c in cases if "speedup" in c and max(c["alg1_ms"], c["bfs_ms"]) >= 0.2]
+    out = {"ablation": "structural reordering (Alg. 1) vs breadth-first order, GPU count, monomorphism",
+           "graphs": len(cases), "measured": len(sp_),
+           "above_0.2ms": {"cases": len(big),
+                           "geomean_speedup": round(math.exp(statistics.mean(math.log(x) for x in big)), 3) if big else None,
+                           "min_speedup": min(big) if big else None},
+           "mean_speedup": round(statistics.mean(sp_), 3) if sp_ else None,
+           "geomean_speedup": round(math.exp(statistics.mean(math.log(x) for x in sp_)), 3) if sp_ else None,
+           "max_speedup": max(sp_) if sp_ else None, "min_speedup": min(sp_) if sp_ else None,
+           "cases": cases}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.ablation:
+        run_ablation(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

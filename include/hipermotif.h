@@ -161,6 +161,16 @@ hm_status hm_graph_export_groups(const hm_graph *g, int32_t *gout_adj, int32_t *
 hm_status hm_load_pattern(int32_t k, int32_t mp, const int32_t *src, const int32_t *dst,
                           const int32_t *vlab, const int32_t *elab, hm_pattern **out);
 
+/* hm_load_pattern_ordered -- as hm_load_pattern, but the visiting order is
+ * the caller's instead of Alg. 1's (for ablations of the reordering,
+ * Sec. IV-C): order (HOST int32[k]) lists the original vertex at each
+ * position.  It must be a permutation (else HM_ERR_ARG) in which every
+ * position after the first has an arc, in either direction, to an earlier
+ * position (else HM_ERR_PATTERN).  Results never depend on the order. */
+hm_status hm_load_pattern_ordered(int32_t k, int32_t mp, const int32_t *src, const int32_t *dst,
+                                  const int32_t *vlab, const int32_t *elab, const int32_t *order,
+                                  hm_pattern **out);
+
 void hm_free_pattern(hm_pattern *p);
 
 /* order_out (host int32[k]) receives Alg. 1's result: order_out[i] is the

@@ -136,19 +136,27 @@ class Graph:
 class Pattern:
     """A pattern graph after Alg. 1; host-only (needs no GPU)."""
 
-    def __init__(self, k: int, src, dst, vlab, elab):
+    def __init__(self, k: int, src, dst, vlab, elab, order=None):
+        """`order` (optional): the original vertex at each position, replacing Alg. 1's order."""
         keep = [_host_i32(a) for a in (src, dst, vlab, elab)]
         h = ctypes.c_void_p()
-        st = lib.hm_load_pattern(int(k), int(keep[0].shape[0]), *[_ptr(a) for a in keep],
-                                 ctypes.byref(h))
+        if order is None:
+            st = lib.hm_load_pattern(int(k), int(keep[0].shape[0]), *[_ptr(a) for a in keep],
+                                     ctypes.byref(h))
+        else:
+            o = _host_i32(order)
+            if o.shape[0] != int(k):
+                raise ValueError("order must list k vertices")
+            st = lib.hm_load_pattern_ordered(int(k), int(keep[0].shape[0]), *[_ptr(a) for a in keep],
+                                             _ptr(o), ctypes.byref(h))
         check(st, "hm_load_pattern")
         self._h = h
         self.k = int(k)
         self.mp = int(keep[0].shape[0])
 
     @classmethod
-    def from_synth(cls, p):
-        return cls(p.k, p.src, p.dst, p.vlab, p.elab)
+    def from_synth(cls, p, order=None):
+        return cls(p.k, p.src, p.dst, p.vlab, p.elab, order=order)
 
     @classmethod
     def with_properties(cls, g: "Graph", k: int, src, dst, vprops, eprops):

@@ -28,6 +28,7 @@ EXPORTED = [
     "hm_set_tuning", "hm_get_tuning", "hm_count_batch", "hm_enumerate_batch", "hm_autotune",
     "hm_server_create", "hm_server_submit", "hm_server_poll", "hm_server_release",
     "hm_server_stats", "hm_server_destroy", "hm_load_graph_props", "hm_load_pattern_props",
+    "hm_load_pattern_ordered",
 ]
 
 
@@ -94,6 +95,7 @@ _SIGS = {
     "hm_graph_export": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hm_graph_export_groups": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hm_load_pattern": (_st, [_i32, _i32, _vp, _vp, _vp, _vp, _pvp]),
+    "hm_load_pattern_ordered": (_st, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _pvp]),
     "hm_load_graph_props": (_st, [_i32, _i64, _vp, _vp, _i32, _vp, _i32, _vp, _vp, _pvp]),
     "hm_load_pattern_props": (_st, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _pvp]),
     "hm_free_pattern": (None, [_vp]),

@@ -200,6 +200,48 @@ extern "C" hm_status hm_load_pattern(int32_t k, int32_t mp, const int32_t *src,
   return HM_OK;
 }
 
+extern "C" hm_status hm_load_pattern_ordered(int32_t k, int32_t mp, const int32_t *src,
+                                             const int32_t *dst, const int32_t *vlab,
+                                             const int32_t *elab, const int32_t *order,
+                                             hm_pattern **out) {
+  if (!order) return HM_ERR_ARG;
+  hm_pattern *p = nullptr;
+  hm_status st = hm_load_pattern(k, mp, src, dst, vlab, elab, &p);  // validation + Alg. 1
+  if (st != HM_OK) return st;
+  PatternGraph P;
+  P.k = k;
+  for (int i = 0; i < k; ++i) P.vlab[i] = vlab[i];
+  for (int e = 0; e < mp; ++e) {
+    P.arc[src[e]][dst[e]] = true;
+    P.lab[src[e]][dst[e]] = elab[e];
+    P.outdeg[src[e]]++;
+    P.indeg[dst[e]]++;
+  }
+  // the given order must be a permutation in which every position after the
+  // first has an arc (either direction) to an earlier position
+  bool seen[HM_MAX_K] = {};
+  for (int i = 0; i < k; ++i) {
+    const int v = order[i];
+    if (v < 0 || v >= k || seen[v]) {
+      hm_free_pattern(p);
+      return HM_ERR_ARG;
+    }
+    bool anchored = i == 0;
+    for (int j = 0; j < i; ++j)
+      if (P.arc[v][order[j]] || P.arc[order[j]][v]) anchored = true;
+    if (!anchored) {
+      hm_free_pattern(p);
+      return HM_ERR_PATTERN;
+    }
+    seen[v] = true;
+  }
+  for (int i = 0; i < k; ++i) p->order[i] = order[i];
+  build_plan(P, p->order, 0, p->plan[0]);
+  build_plan(P, p->order, 1, p->plan[1]);
+  *out = p;
+  return HM_OK;
+}
+
 extern "C" void hm_free_pattern(hm_pattern *p) { delete p; }
 
 extern "C" hm_status hm_pattern_order(const hm_pattern *p, int32_t *order_out) {

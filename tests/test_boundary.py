@@ -124,3 +124,34 @@ def test_tuning_defaults_roundtrip(hm):
     hm.set_tuning()
     assert hm.get_tuning() == dict(extend_min_blocks=5, split_min=64, pair_mode=0, seeds_per_fetch=1,
                                    poll_every=128, leaf_flatten=1)
+
+
+def _bfs_order(k, src, dst):
+    adj = {v: set() for v in range(k)}
+    for a, b in zip(src, dst):
+        adj[int(a)].add(int(b))
+        adj[int(b)].add(int(a))
+    order, seen = [0], {0}
+    for v in order:
+        for w in sorted(adj[v]):
+            if w not in seen:
+                seen.add(w)
+                order.append(w)
+    return order
+
+
+def test_pattern_with_a_given_order(hm):
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        k = int(rng.integers(2, 12))
+        p = synth.random_pattern(rng, k, 0.4, n_vlab=2, n_elab=2)
+        order = _bfs_order(k, p.src, p.dst)
+        assert hm.Pattern.from_synth(p, order=order).order == order
+    p = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
+                      np.zeros(3, np.int32), np.zeros(2, np.int32))
+    with pytest.raises(hm.HMError) as ei:                       # position 1 unanchored
+        hm.Pattern.from_synth(p, order=[0, 2, 1])
+    assert ei.value.status == hm.binding.HM_ERR_PATTERN
+    with pytest.raises(hm.HMError) as ei:                       # not a permutation
+        hm.Pattern.from_synth(p, order=[0, 1, 1])
+    assert ei.value.status == hm.binding.HM_ERR_ARG

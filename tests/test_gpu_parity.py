@@ -406,3 +406,21 @@ def test_tuning_knobs_never_change_results(hm, knobs):
             _check(hm, G, og, sp, oracle.MONO, rows=False)
     finally:
         hm.set_tuning()
+
+
+def test_results_do_not_depend_on_the_order(hm):
+    """The reordering is a heuristic: breadth-first order gives the same sorted rows as Alg. 1's."""
+    from tests.test_boundary import _bfs_order
+
+    g = synth.config2_graph(scale=12)
+    G = hm.Graph.from_synth(g)
+    rng = np.random.default_rng(31)
+    for _ in range(12):
+        sp = synth.random_pattern(rng, int(rng.integers(3, 8)), float(rng.uniform(0.3, 0.8)),
+                                  n_vlab=3, n_elab=2)
+        P1 = hm.Pattern.from_synth(sp)
+        P2 = hm.Pattern.from_synth(sp, order=_bfs_order(sp.k, sp.src, sp.dst))
+        for mode in MODES:
+            a = hm.enumerate_matches(G, P1, mode).cpu().numpy()
+            b = hm.enumerate_matches(G, P2, mode).cpu().numpy()
+            np.testing.assert_array_equal(a, b)
