@@ -181,34 +181,82 @@ def _discrete_power_law(rng, count, exponent, dmin, dmax) -> np.ndarray:
     return support[rng.choice(support.shape[0], size=count, p=pmf)]
 
 
+def _alias_table(weights: np.ndarray):
+    """Walker's alias method (Vose's construction): O(1) draws proportional to `weights`."""
+    n = weights.shape[0]
+    scaled = weights.astype(np.float64) * (n / weights.sum())
+    prob = np.ones(n, dtype=np.float64)
+    alias = np.arange(n, dtype=np.int64)
+    small = np.nonzero(scaled < 1.0)[0].tolist()
+    large = np.nonzero(scaled >= 1.0)[0].tolist()
+    sc = scaled.tolist()
+    while small and large:
+        s_, l_ = small.pop(), large.pop()
+        prob[s_] = sc[s_]
+        alias[s_] = l_
+        sc[l_] = sc[l_] + sc[s_] - 1.0
+        (small if sc[l_] < 1.0 else large).append(l_)
+    return prob, alias
+
+
+def _alias_draw(rng, table, count: int) -> np.ndarray:
+    prob, alias = table
+    i = rng.integers(0, prob.shape[0], size=count, dtype=np.int64)
+    return np.where(rng.random(count) < prob[i], i, alias[i])
+
+
+def _merge_unique(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Distinct keys of two ascending arrays, ascending (one stable run-merging sort)."""
+    keys = np.concatenate([a, b])
+    keys.sort(kind="stable")
+    if keys.shape[0] == 0:
+        return keys
+    keep = np.empty(keys.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+    return keys[keep]
+
+
 def chung_lu_graph(n: int, exponent: float, dmin: int, dmax: int, n_unique: int,
                    n_recip: int, vlab_weights, n_elab: int, seed: int) -> Graph:
     """Directed Chung-Lu graph with power-law in- and out-weights and added reciprocity.
 
     Out- and in-weights are drawn independently from a discrete power law
-    proportional to d^-exponent on [dmin, dmax].  Arcs are drawn with source
-    proportional to the out-weight and destination proportional to the
-    in-weight; self-loops are dropped and the first `n_unique` distinct arcs
-    are kept.  Then `n_recip` of those arcs are chosen uniformly and their
-    reverses added (reverses already present are not duplicated).
+    proportional to d^-exponent on [dmin, dmax].  Arcs are drawn (alias tables)
+    with source proportional to the out-weight and destination proportional to
+    the in-weight, self-loops dropped, until at least `n_unique` distinct arcs
+    exist; a seeded uniform subset of exactly `n_unique` of them is kept.  Then
+    `n_recip` of those arcs are chosen uniformly and their reverses added
+    (reverses already present are not duplicated).
     """
     rng = _rng(seed)
     w_out = _discrete_power_law(rng, n, exponent, dmin, dmax)
     w_in = _discrete_power_law(rng, n, exponent, dmin, dmax)
-    cdf_out = np.cumsum(w_out / w_out.sum())
-    cdf_in = np.cumsum(w_in / w_in.sum())
-    cdf_out[-1] = cdf_in[-1] = 1.0
+    t_out, t_in = _alias_table(w_out), _alias_table(w_in)
     keys = np.empty(0, dtype=np.int64)
+    chunk = 1 << 24
     while keys.shape[0] < n_unique:
-        b = int(1.15 * (n_unique - keys.shape[0])) + 1024
-        u = np.searchsorted(cdf_out, rng.random(b), side="right").astype(np.int64)
-        v = np.searchsorted(cdf_in, rng.random(b), side="right").astype(np.int64)
-        keep = u != v
-        keys = _first_unique(np.concatenate([keys, u[keep] * n + v[keep]]))
-    keys = keys[:n_unique]
+        want = int(1.1 * (n_unique - keys.shape[0])) + 1024
+        parts = []
+        for lo in range(0, want, chunk):
+            b = min(chunk, want - lo)
+            u = _alias_draw(rng, t_out, b)
+            v = _alias_draw(rng, t_in, b)
+            k = u[u != v] * n + v[u != v]
+            k.sort()
+            parts.append(k)
+        new = np.concatenate(parts)
+        new.sort(kind="stable")
+        keys = _merge_unique(keys, new)
+    excess = keys.shape[0] - n_unique
+    if excess > 0:
+        keep = np.ones(keys.shape[0], dtype=bool)
+        keep[rng.choice(keys.shape[0], size=excess, replace=False)] = False
+        keys = keys[keep]
     pick = rng.choice(keys.shape[0], size=n_recip, replace=False)
     rev = (keys[pick] % n) * n + keys[pick] // n
-    keys = _sorted_unique(np.concatenate([keys, rev]))
+    rev.sort()
+    keys = _merge_unique(keys, rev)
     src, dst = keys // n, keys % n
     vlab = _labels(rng, n, weights=vlab_weights)
     elab = _labels(rng, keys.shape[0], n_values=n_elab)
@@ -388,11 +436,15 @@ def config5_arrivals(rate: float, count: int, seed: int = 4, n_vlab: int = 6, n_
 # on-disk cache for the large graphs (pure function of the arguments)
 # ---------------------------------------------------------------------------
 
+#: bumped whenever a generator's output changes, so stale cache files are not reused
+_GENERATOR_VERSION = 2
+
+
 def cached(name: str, fn, *args, **kwargs) -> Graph:
     """Return fn(*args, **kwargs), memoised as an .npz under $HM_CACHE (default /tmp/hm_cache)."""
     root = os.environ.get("HM_CACHE", "/tmp/hm_cache")
     os.makedirs(root, exist_ok=True)
-    key = name + "_" + "_".join(str(a) for a in args) + "_" + "_".join(
+    key = f"{name}_v{_GENERATOR_VERSION}_" + "_".join(str(a) for a in args) + "_" + "_".join(
         f"{k}{v}" for k, v in sorted(kwargs.items()))
     path = os.path.join(root, key + ".npz")
     if os.path.exists(path):

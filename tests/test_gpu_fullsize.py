@@ -1,0 +1,205 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times.
+
+At full size the oracle cannot enumerate everything in a test's time, so each
+workload is checked three ways:
+
+* sampled outputs: the GPU's rows whose image of original pattern vertex 0
+  lies in a seeded random root set S must equal, element by element, the
+  oracle's rows restricted to the same S (the oracle's root mask);
+* properties that hold at any size: rows strictly ascending (so distinct and
+  in the contract's order), the row count equal to the count call, and a
+  seeded sample of rows re-checked against the definition (labels, arcs and,
+  for induced matching, non-arcs) with plain numpy lookups;
+* consistency between entry points: rooted counts over a partition of the
+  vertices sum to the full count; batched and served results equal the
+  single-query calls.
+
+Workloads: R-MAT scale 20 with the three induced 4-vertex motifs; the
+connectome-shaped graph (300k vertices, ~150M arcs) with five 5-vertex
+monomorphism patterns; 256 random patterns batched against the R-MAT graph;
+served Poisson arrivals against the R-MAT graph.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2507_04130_gb300 as mod
+    assert torch.cuda.is_available()
+    mod.set_budget(120_000, 0)
+    mod.set_tuning()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def rmat(hm):
+    g = synth.cached("rmat", synth.config2_graph, scale=20)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    yield g, G, og
+    G.close()
+    og.close()
+
+
+def _root_mask(n, frac, seed):
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(n, np.uint8)
+    mask[rng.permutation(n)[: max(1, int(frac * n))]] = 1
+    return mask
+
+
+def _strictly_ascending(rows: np.ndarray):
+    if rows.shape[0] < 2:
+        return
+    a, b = rows[:-1], rows[1:]
+    diff = a != b
+    first = np.argmax(diff, axis=1)
+    assert diff.any(axis=1).all(), "duplicate rows"
+    idx = np.arange(a.shape[0])
+    assert np.all(a[idx, first] < b[idx, first]), "rows out of lexicographic order"
+
+
+class _ArcTable:
+    """Sorted (src*n + dst) keys with their labels: exact arc lookups in numpy."""
+
+    def __init__(self, g):
+        self.n = g.n
+        keys = g.src.astype(np.int64) * g.n + g.dst
+        order = np.argsort(keys, kind="stable")
+        self.keys = keys[order]
+        self.elab = g.elab[order]
+        self.vlab = g.vlab
+
+    def lookup(self, a, b):
+        q = a.astype(np.int64) * self.n + b
+        i = np.searchsorted(self.keys, q)
+        i = np.minimum(i, self.keys.shape[0] - 1)
+        present = self.keys[i] == q
+        return present, np.where(present, self.elab[i], -1)
+
+
+def _check_rows_by_definition(table, sp, mode, rows):
+    """Each row is injective, keeps vertex labels, maps arcs onto arcs of equal
+    label and (induced) non-arcs onto non-arcs."""
+    if rows.shape[0] == 0:
+        return
+    k = sp.k
+    s = np.sort(rows, axis=1)
+    assert np.all(s[:, 1:] != s[:, :-1]), "a row maps two pattern vertices to one target vertex"
+    for p in range(k):
+        assert np.all(table.vlab[rows[:, p]] == sp.vlab[p])
+    arcs = {(int(a), int(b)): int(l) for a, b, l in zip(sp.src, sp.dst, sp.elab)}
+    for a in range(k):
+        for b in range(k):
+            if a == b:
+                continue
+            present, lab = table.lookup(rows[:, a], rows[:, b])
+            if (a, b) in arcs:
+                assert present.all() and np.all(lab == arcs[(a, b)])
+            elif mode == oracle.INDUCED:
+                assert not present.any()
+
+
+def test_rmat_motifs_full_size(hm, rmat):
+    """The benchmark's three induced motifs on R-MAT scale 20, its exact call."""
+    g, G, og = rmat
+    table = _ArcTable(g)
+    mask = _root_mask(g.n, 0.04, seed=11)
+    rng = np.random.default_rng(5)
+    total = 0
+    for sp in synth.config2_patterns():
+        P = hm.Pattern.from_synth(sp)
+        c = hm.count_matches_part(G, P, hm.INDUCED, 0, 1)
+        buf = torch.empty(max(c, 1) * sp.k, dtype=torch.int32, device="cuda")
+        rows = hm.enumerate_matches_part(G, P, hm.INDUCED, 0, 1, buf).cpu().numpy()
+        assert rows.shape == (c, sp.k)
+        total += c
+        _strictly_ascending(rows)
+        sample = rows[rng.integers(0, rows.shape[0], 200_000)] if rows.shape[0] else rows
+        _check_rows_by_definition(table, sp, oracle.INDUCED, sample)
+        want_c, want_rows = og.match(sp, oracle.INDUCED, rows=True, root_mask=mask)
+        mine = rows[mask[rows[:, 0]] == 1]
+        assert mine.shape[0] == want_c > 0
+        np.testing.assert_array_equal(mine, want_rows)
+    assert total > 1_000_000
+
+
+def test_batched_256_full_size(hm, rmat):
+    """256 random induced patterns in one batched launch against R-MAT scale 20."""
+    g, G, og = rmat
+    pats = synth.config4_patterns()
+    P = [hm.Pattern.from_synth(p) for p in pats]
+    counts = hm.count_batch(G, P, hm.INDUCED)
+    rows = hm.enumerate_batch(G, P, hm.INDUCED, counts=counts)
+    mask = _root_mask(g.n, 0.02, seed=12)
+    rng = np.random.default_rng(6)
+    checked = 0
+    for i in rng.permutation(len(pats))[:96]:
+        sp, r = pats[i], rows[i].cpu().numpy()
+        assert r.shape == (counts[i], sp.k)
+        _strictly_ascending(r)
+        want_c, want_rows = og.match(sp, oracle.INDUCED, rows=True, root_mask=mask)
+        mine = r[mask[r[:, 0]] == 1]
+        np.testing.assert_array_equal(mine, want_rows)
+        checked += want_c
+    assert checked > 0
+    # one batch equals the single-pattern calls, for a seeded subset
+    for i in rng.permutation(len(pats))[:24]:
+        assert hm.count_matches(G, P[i], hm.INDUCED) == counts[i]
+
+
+def test_served_arrivals_full_size(hm, rmat):
+    """Queries served concurrently (mixed modes, uneven sizes) return what each returns alone."""
+    g, G, og = rmat
+    arrivals = synth.config5_arrivals(300, 48, n_vlab=8, n_elab=4)
+    srv = hm.Server(G, slots=4, max_batch=16)
+    try:
+        ids = [srv.submit(p, mode, want_rows=True) for _, p, mode in arrivals]
+        res = [srv.result(q) for q in ids]
+    finally:
+        srv.close()
+    mask = _root_mask(g.n, 0.02, seed=13)
+    for (_, sp, mode), r in zip(arrivals, res):
+        P = hm.Pattern.from_synth(sp)
+        assert r["count"] == hm.count_matches(G, P, mode)
+        assert not r["rows_dropped"]
+        rows = r["rows"] if r["rows"] is not None else np.zeros((0, sp.k), np.int32)
+        assert rows.shape == (r["count"], sp.k)
+        _strictly_ascending(rows)
+        want_c, want_rows = og.match(sp, mode, rows=True, root_mask=mask)
+        np.testing.assert_array_equal(rows[mask[rows[:, 0]] == 1], want_rows)
+
+
+def test_connectome_full_size(hm):
+    """Five 5-vertex monomorphism patterns on the ~150M-arc connectome-shaped graph."""
+    g = synth.cached("conn", synth.config3_graph)
+    assert g.m > 140_000_000
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    try:
+        masks = [_root_mask(g.n, 0.02, seed=20 + i) for i in range(3)]
+        part = np.random.default_rng(21).integers(0, 4, g.n)
+        for sp in synth.config3_patterns():
+            P = hm.Pattern.from_synth(sp)
+            full = hm.count_matches(G, P, hm.MONO)
+            for mask in masks:
+                got = hm.count_matches_rooted(G, P, hm.MONO, 0, mask)
+                assert got == og.match(sp, oracle.MONO, rows=False, root_mask=mask)[0]
+            s = sum(hm.count_matches_rooted(G, P, hm.MONO, 0, (part == i).astype(np.uint8))
+                    for i in range(4))
+            assert s == full
+    finally:
+        G.close()
+        og.close()
