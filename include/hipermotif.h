@@ -362,6 +362,10 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      ranges are swept together in full 32-lane chunks
  *                      (survivors with more than 2048 leaf candidates take the
  *                      ordinary path); -1: one survivor at a time.
+ *   arc_filter         a membership test ("is (x, y) an arc?", "is there no
+ *                      arc?") that would search more than this many sorted
+ *                      entries first probes the graph's arc filter, a Bloom
+ *                      filter whose "no" is exact (default 4; -1: never).
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -371,6 +375,7 @@ typedef struct {
   int32_t seeds_per_fetch;
   int32_t poll_every;
   int32_t leaf_flatten;
+  int32_t arc_filter;
 } hm_tuning;
 
 hm_status hm_set_tuning(const hm_tuning *t);

@@ -72,6 +72,7 @@ class hm_tuning(ctypes.Structure):
         ("seeds_per_fetch", ctypes.c_int32),
         ("poll_every", ctypes.c_int32),
         ("leaf_flatten", ctypes.c_int32),
+        ("arc_filter", ctypes.c_int32),
     ]
 
     def as_dict(self):

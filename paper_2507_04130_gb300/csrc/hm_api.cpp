@@ -5,6 +5,7 @@
 
 namespace hm {
 namespace {
+constexpr int kDefaultFilterMin = 4;
 std::atomic<uint64_t> g_budget_ms{120000};
 std::atomic<uint64_t> g_budget_chunks{0};
 std::atomic<int> g_timing{0};
@@ -12,6 +13,7 @@ std::atomic<int> g_counters{0};
 std::atomic<int> g_min_blocks{5}, g_split_min{64}, g_pair_mode{0}, g_seeds_per_fetch{1};
 std::atomic<int> g_poll_every{128};
 std::atomic<int> g_leaf_flatten{1};
+std::atomic<int> g_arc_filter{kDefaultFilterMin};
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -28,8 +30,10 @@ hm_tuning tuning() {
   t.seeds_per_fetch = g_seeds_per_fetch.load(std::memory_order_relaxed);
   t.poll_every = g_poll_every.load(std::memory_order_relaxed);
   t.leaf_flatten = g_leaf_flatten.load(std::memory_order_relaxed);
+  t.arc_filter = g_arc_filter.load(std::memory_order_relaxed);
   return t;
 }
+int32_t filter_min() { return g_arc_filter.load(std::memory_order_relaxed); }
 uint64_t budget_ms() { return g_budget_ms.load(std::memory_order_relaxed); }
 uint64_t budget_chunks() { return g_budget_chunks.load(std::memory_order_relaxed); }
 }  // namespace hm
@@ -80,7 +84,7 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   const int pe = t->poll_every ? t->poll_every : 128;
   if ((mb != 5 && mb != 6 && mb != 8) || sm < 2 || sp < 1 || sp > 1024 ||
       (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)) ||
-      t->leaf_flatten < -1 || t->leaf_flatten > 1)
+      t->leaf_flatten < -1 || t->leaf_flatten > 1 || t->arc_filter < -1)
     return HM_ERR_ARG;
   hm::g_min_blocks.store(mb);
   hm::g_split_min.store(sm);
@@ -88,6 +92,7 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   hm::g_seeds_per_fetch.store(sp);
   hm::g_poll_every.store(pe);
   hm::g_leaf_flatten.store(t->leaf_flatten < 0 ? -1 : 1);
+  hm::g_arc_filter.store(t->arc_filter ? t->arc_filter : hm::kDefaultFilterMin);
   return HM_OK;
 }
 

@@ -478,7 +478,7 @@ extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *pat
     if (budget_ms && spent > (double)budget_ms) break;
   }
   hm_set_tuning(&pick);
-  *best = pick;
+  hm_get_tuning(best);  // with the defaults filled in
   if (best_ms) *best_ms = (float)best_t;
   return HM_OK;
 }

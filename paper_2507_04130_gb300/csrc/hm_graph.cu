@@ -14,6 +14,7 @@
 //      (vertex, arc label, neighbour label) group                (k_group_*)
 //   4. the same for in-lists, keyed on dst (steps 2-3 mirrored)
 //   5. per-vertex records {label, degrees}, {offsets}, {directory spans}
+//   6. the arc filter: every arc sets its eight bits              (k_filter)
 // The grouped lists let the extension kernel jump straight to the candidates
 // whose arc label and vertex label already match (checkAttributes of Alg. 2
 // and Alg. 3 applied as a range lookup instead of per candidate).
@@ -162,6 +163,17 @@ __global__ void k_vertex(const int32_t *__restrict__ vlab, const int64_t *__rest
   }
 }
 
+__global__ void k_filter(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m,
+                         uint32_t nblk, uint32_t *__restrict__ words) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const FilterSlot f = filter_slot(src[e], dst[e], nblk);
+    uint32_t *w = words + 8 * (size_t)f.blk;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) atomicOr(w + i, 1u << ((f.bits >> (5 * i)) & 31));
+  }
+}
+
 int grid_for(int64_t work) {
   int64_t g = (work + kThreads - 1) / kThreads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)num_sms() * 16));
@@ -300,6 +312,9 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
   HM_CUDA_TRY(dmalloc(&g->vi, n));
   HM_CUDA_TRY(dmalloc(&g->off, n));
   HM_CUDA_TRY(dmalloc(&g->vdir, n));
+  g->afilt_nblk = (uint32_t)std::max<int64_t>(1, (m + 15) / 16);
+  HM_CUDA_TRY(dmalloc(&g->afilt, 2 * (int64_t)g->afilt_nblk));
+  HM_CUDA_TRY(cudaMemsetAsync(g->afilt, 0, 32 * (size_t)g->afilt_nblk, s));
 
   const int nbits = bits_for(n);
   int be = 1, bv = 1;
@@ -314,6 +329,8 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
     if (st != HM_OK) return st;
     k_split<<<grid_for(m), kThreads, 0, s>>>(rows, m, n, 0, 1, g->src, g->out_adj, g->out_elab,
                                              out_off, err);
+    k_filter<<<grid_for(m), kThreads, 0, s>>>(g->src, g->out_adj, m, g->afilt_nblk,
+                                              reinterpret_cast<uint32_t *>(g->afilt));
     st = build_groups(rows, tmp, m, n, 0, 1, d_vlab, out_off, nbits, be, xe, bv, xv, s, T,
                       &g->gout_adj, &g->gdir_out, &g->ndir_out, &oidx);
     if (st != HM_OK) return st;
@@ -340,13 +357,14 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
   HM_CUDA_TRY(cudaGetLastError());
   if (h_err & kErrDup) return HM_ERR_DUP_EDGE;
   g->bytes = sizeof(int32_t) * 7 * (size_t)m + (sizeof(int4) * 2 + sizeof(int2)) * (size_t)n +
-             sizeof(int4) * (size_t)(g->ndir_out + g->ndir_in);
+             sizeof(int4) * (size_t)(g->ndir_out + g->ndir_in) + 32 * (size_t)g->afilt_nblk;
   return HM_OK;
 }
 
 void free_graph_arrays(hm_graph *g) {
   void *ptrs[] = {g->src,     g->out_adj,  g->out_elab, g->in_adj,   g->in_elab, g->vi,
-                  g->off,     g->gout_adj, g->gin_adj,  g->gdir_out, g->gdir_in, g->vdir};
+                  g->off,     g->gout_adj, g->gin_adj,  g->gdir_out, g->gdir_in, g->vdir,
+                  g->afilt};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }

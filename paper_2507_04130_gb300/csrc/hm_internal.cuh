@@ -9,6 +9,8 @@
 //   in_elab  int32[m]  label of each in-arc, parallel to in_adj
 //   vi       int4[n]   {vertex label, out-degree, in-degree, 0}
 //   off      int2[n]   {first out-arc, first in-arc}   (m < 2^31, so 32-bit offsets)
+//   afilt    uint4[2*B] arc-existence filter: B = ceil(m/16) blocks of 256 bits
+//                      (16 bits per arc; 32 MB for 16M arcs, so it stays in L2)
 // A vertex's label and both degrees arrive in one 16-byte load; its list
 // offsets in a second one, fetched only when a list is actually searched.
 #pragma once
@@ -22,6 +24,7 @@ namespace hm {
 
 constexpr int kMaxK = HM_MAX_K;
 constexpr int kMaxCons = 2 * (HM_MAX_K - 1);
+static_assert(kMaxCons <= 64, "condition masks are 64-bit");
 constexpr int kWarp = 32;
 
 struct DevGraph {
@@ -41,6 +44,12 @@ struct DevGraph {
   const int4 *gdir_out;  // {arc label, neighbour label, first, end} (relative to the list start)
   const int4 *gdir_in;
   const int4 *vdir;      // {first out entry, out entries, first in entry, in entries}
+  // split-block Bloom filter over the arcs (u, v), labels ignored: a "no" is
+  // exact, a "maybe" needs the search.  Searches over more than filt_min
+  // entries probe it first (filt_min < 0: never).
+  const uint4 *afilt;
+  uint32_t afilt_nblk;
+  int32_t filt_min;
 };
 
 // One pairwise condition between the position being extended (p) and an
@@ -145,6 +154,46 @@ __device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32
   }
 }
 
+// ---- arc filter -------------------------------------------------------------
+// Each arc (u, v) owns one 256-bit block (eight 32-bit words) chosen by a hash
+// of the pair and sets one bit in each word, at positions from a second hash.
+// Both hashes are the splitmix64 finalizer (Steele, Lea and Flood, "Fast
+// splittable pseudorandom number generators", OOPSLA 2014).  With 16 bits per
+// arc a pair that is not an arc passes all eight bits with probability about
+// 0.1 %; an arc always passes.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+struct FilterSlot {
+  uint32_t blk;   // block index
+  uint64_t bits;  // eight 5-bit positions, word i at bits [5i, 5i+5)
+};
+
+__host__ __device__ __forceinline__ FilterSlot filter_slot(int32_t u, int32_t v, uint32_t nblk) {
+  const uint64_t h = mix64(((uint64_t)(uint32_t)u << 32) | (uint32_t)v);
+  FilterSlot f;
+  f.blk = (uint32_t)(((h >> 32) * (uint64_t)nblk) >> 32);
+  f.bits = mix64(h ^ 0x5851f42d4c957f2dull);
+  return f;
+}
+
+// false: (u, v) is certainly not an arc.  true: it may be.
+template <bool kCount>
+__device__ __forceinline__ bool arc_maybe(const DevGraph &G, int32_t u, int32_t v, uint64_t &bytes) {
+  const FilterSlot f = filter_slot(u, v, G.afilt_nblk);
+  const uint4 a = __ldg(G.afilt + 2 * (size_t)f.blk);
+  const uint4 b = __ldg(G.afilt + 2 * (size_t)f.blk + 1);
+  if (kCount) bytes += 32;
+  const uint64_t x = f.bits;
+  const uint32_t t = (a.x >> (x & 31)) & (a.y >> ((x >> 5) & 31)) & (a.z >> ((x >> 10) & 31)) &
+                     (a.w >> ((x >> 15) & 31)) & (b.x >> ((x >> 20) & 31)) &
+                     (b.y >> ((x >> 25) & 31)) & (b.z >> ((x >> 30) & 31)) & (b.w >> ((x >> 35) & 31));
+  return t & 1u;
+}
+
 __device__ __forceinline__ int32_t search(const int32_t *__restrict__ a, int32_t lo, int32_t len,
                                           int32_t x) {
   uint64_t unused = 0;
@@ -170,6 +219,10 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // host-side objects
 // ---------------------------------------------------------------------------
 
+namespace hm {
+int32_t filter_min();  // current search length above which the arc filter is probed first
+}
+
 struct hm_graph {
   int device;
   int32_t n;
@@ -179,6 +232,8 @@ struct hm_graph {
   int2 *off;
   int32_t *gout_adj, *gin_adj;
   int4 *gdir_out, *gdir_in, *vdir;
+  uint4 *afilt;
+  uint32_t afilt_nblk;
   int64_t ndir_out, ndir_in;
   size_t bytes;
   // multi-property graphs (hm_load_graph_props): the sorted distinct property
@@ -187,8 +242,9 @@ struct hm_graph {
   int64_t nvtab, netab;
   int32_t *vtab, *etab;
   hm::DevGraph dev() const {
-    return hm::DevGraph{n,        m,       src,      out_adj,  out_elab, in_adj, in_elab, vi,
-                        off,      gout_adj, gin_adj, gdir_out, gdir_in,  vdir};
+    return hm::DevGraph{n,        m,        src,     out_adj,  out_elab, in_adj,     in_elab,
+                        vi,       off,      gout_adj, gin_adj, gdir_out, gdir_in,    vdir,
+                        afilt,    afilt_nblk, hm::filter_min()};
   }
 };
 

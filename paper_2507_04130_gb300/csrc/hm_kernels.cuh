@@ -133,6 +133,11 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t *p) {
   return *(const volatile int32_t *)p;
 }
 
+// Is a search over `len` sorted entries long enough to ask the arc filter first?
+__device__ __forceinline__ bool use_filter(const DevGraph &G, int32_t len) {
+  return G.filt_min >= 0 && len > G.filt_min;
+}
+
 // ---------------------------------------------------------------------------
 // arc lookup: is (x -> y) an arc?  Searches the shorter of out(x) and in(y).
 // ---------------------------------------------------------------------------
@@ -140,6 +145,7 @@ template <bool kC>
 __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t y, int32_t outdeg_x,
                                            int32_t indeg_y, int32_t *lab, uint64_t &ctr) {
   if (outdeg_x == 0 || indeg_y == 0) return false;
+  if (use_filter(G, min(outdeg_x, indeg_y)) && !arc_maybe<kC>(G, x, y, ctr)) return false;
   if (kC) ctr += 8;
   if (outdeg_x <= indeg_y) {
     const int32_t o = __ldg(&G.off[x].x);
@@ -268,8 +274,11 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
 template <bool kC>
 __device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, int2 oy,
                                         int32_t w, uint64_t &ctr) {
-  if (iy.y && search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0) return true;
-  return iy.z && search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0;
+  if (iy.y && (!use_filter(G, iy.y) || arc_maybe<kC>(G, y, w, ctr)) &&
+      search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0)
+    return true;
+  return iy.z && (!use_filter(G, iy.z) || arc_maybe<kC>(G, w, y, ctr)) &&
+         search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0;
 }
 
 // In batched launches (kB) each seed carries its pattern id; the threshold is
@@ -479,6 +488,8 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int2 r = grp[P.gbase[p] + j];
       const int32_t rev_len = fwd ? vi.z : vi.y;
       if (r.y == 0) return false;
+      if (use_filter(G, min(rev_len, r.y)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr))
+        return false;
       if (rev_len < r.y) {
         const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
                               : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
@@ -494,6 +505,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
       const int32_t lb = fwd ? vi.z : vi.y;
       if (la == 0 || lb == 0) continue;
+      if (use_filter(G, min(la, lb)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr)) continue;
       if (la <= lb) {
         found = search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) >= 0;
       } else {
@@ -529,6 +541,8 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
     const int2 r = grp[P.gbase[p] + j];
     const int32_t rev_len = fwd ? vi.z : vi.y;
     if (r.y == 0 || rev_len == 0) return false;
+    if (use_filter(G, min(rev_len, r.y)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr))
+      return false;
     if (rev_len < r.y) {
       if (kC) ctr += 16;
       const int2 oc = __ldg(&G.off[c]);
@@ -543,6 +557,7 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
   const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
   const int32_t lb = fwd ? vi.z : vi.y;
   if (la == 0 || lb == 0) return true;
+  if (use_filter(G, min(la, lb)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr)) return true;
   if (la <= lb)
     return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
   if (kC) ctr += 16;
@@ -579,11 +594,32 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
   if (root_mask && p == P.root_pos && !root_mask[d]) return false;
   const int nc = P.ncons[p];
   if (nc <= 1) return true;
+  // first the arc filter, which needs only the two endpoints: most candidates
+  // fail a positive condition here, and most induced non-arcs are settled
+  uint64_t settled = 0;
+  if (G.filt_min >= 0) {
+    for (int j = 0; j < nc; ++j) {
+      if (j == drive) continue;
+      const Cons cs = P.cons[p][j];
+      const bool mine = cs.q == L;
+      const int32_t fq = mine ? o.c : S.map[cs.q];
+      const bool fwd = cs.kind == kOut || cs.kind == kNotOut;
+      if (cs.kind <= kIn) {
+        const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
+        if (r.y == 0) return false;
+        if (use_filter(G, r.y) && !arc_maybe<kC>(G, fwd ? fq : d, fwd ? d : fq, ctr)) return false;
+      } else {
+        const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[cs.q]) : (mine ? o.deg_in : S.deg_in[cs.q]);
+        if (la == 0 || (use_filter(G, la) && !arc_maybe<kC>(G, fwd ? fq : d, fwd ? d : fq, ctr)))
+          settled |= 1ull << j;
+      }
+    }
+  }
   if (kC) ctr += 32;
   const int4 vi = __ldg(&G.vi[d]);
   const int2 od = __ldg(&G.off[d]);
   for (int j = 0; j < nc; ++j) {
-    if (j == drive) continue;
+    if (j == drive || ((settled >> j) & 1)) continue;
     const Cons cs = P.cons[p][j];
     const int q = cs.q;
     const bool mine = q == L;
