@@ -78,7 +78,13 @@ const char *hm_status_str(hm_status s);
  *   out         receives the new graph; the caller frees it with hm_free_graph.
  * Layout built: out-lists (CSR) sorted by (src, dst) and in-lists (CSC) sorted
  * by (dst, src), each with its arc labels, the CSR-order source array, and per
- * vertex {label, out-degree, in-degree} and {out-offset, in-offset}.
+ * vertex {label, out-degree, in-degree} and {out-offset, in-offset}; copies
+ * of both lists grouped by (arc label, neighbour label) with a directory; an
+ * arc filter (split-block Bloom filter keyed by (u, v) and (u, v, label), 32
+ * bits per arc) and an arc hash table (32 bytes per arc) that replace the
+ * paper's O(log d) edge-attribute lookup by one or two cache-sector reads.
+ * Device memory: 64 bytes per arc, 16 per directory entry (at most 2 per arc)
+ * and 40 per vertex (hm_graph_info reports the total).
  * The input arrays are copied; the caller keeps ownership.  m must be below
  * 2^31.  Errors: HM_ERR_ARG (id out of range, n or m negative, m >= 2^31,
  * NULL array),
@@ -362,10 +368,12 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      ranges are swept together in full 32-lane chunks
  *                      (survivors with more than 2048 leaf candidates take the
  *                      ordinary path); -1: one survivor at a time.
- *   arc_filter         a membership test ("is (x, y) an arc?", "is there no
- *                      arc?") that would search more than this many sorted
- *                      entries first probes the graph's arc filter, a Bloom
- *                      filter whose "no" is exact (default 4; -1: never).
+ *   arc_filter         a membership test ("is (x, y) an arc with label l?",
+ *                      "is there no arc?") over a list of more than this many
+ *                      sorted entries probes the graph's arc filter (a Bloom
+ *                      filter whose "no" is exact) and, on "maybe", its arc
+ *                      hash table, instead of a binary search (default 1;
+ *                      -1: always binary search).
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {

@@ -5,7 +5,7 @@
 
 namespace hm {
 namespace {
-constexpr int kDefaultFilterMin = 4;
+constexpr int kDefaultFilterMin = 1;
 std::atomic<uint64_t> g_budget_ms{120000};
 std::atomic<uint64_t> g_budget_chunks{0};
 std::atomic<int> g_timing{0};

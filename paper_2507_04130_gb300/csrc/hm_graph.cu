@@ -14,7 +14,8 @@
 //      (vertex, arc label, neighbour label) group                (k_group_*)
 //   4. the same for in-lists, keyed on dst (steps 2-3 mirrored)
 //   5. per-vertex records {label, degrees}, {offsets}, {directory spans}
-//   6. the arc filter: every arc sets its eight bits              (k_filter)
+//   6. the arc filter: every arc sets its bits under two keys       (k_filter)
+//   7. the arc hash table: every arc claims a slot                  (k_hash)
 // The grouped lists let the extension kernel jump straight to the candidates
 // whose arc label and vertex label already match (checkAttributes of Alg. 2
 // and Alg. 3 applied as a range lookup instead of per candidate).
@@ -30,7 +31,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kW = 4;  // row width: src, dst, arc label, aux
 
-enum : uint32_t { kErrRange = 1, kErrSelf = 2, kErrDup = 4 };
+enum : uint32_t { kErrRange = 1, kErrSelf = 2, kErrDup = 4, kErrHash = 8 };
 
 struct Bounds {
   int32_t emin, emax, vmin, vmax;
@@ -163,14 +164,47 @@ __global__ void k_vertex(const int32_t *__restrict__ vlab, const int64_t *__rest
   }
 }
 
-__global__ void k_filter(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m,
-                         uint32_t nblk, uint32_t *__restrict__ words) {
+__device__ __forceinline__ void filter_insert(uint64_t h, uint32_t nblk, uint32_t *__restrict__ words) {
+  const FilterSlot f = filter_slot_of(h, nblk);
+  uint32_t *w = words + 8 * (size_t)f.blk;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) atomicOr(w + i, 1u << ((f.bits >> (5 * i)) & 31));
+}
+
+__global__ void k_filter(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                         const int32_t *__restrict__ elab, int64_t m, uint32_t nblk,
+                         uint32_t *__restrict__ words) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const FilterSlot f = filter_slot(src[e], dst[e], nblk);
-    uint32_t *w = words + 8 * (size_t)f.blk;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) atomicOr(w + i, 1u << ((f.bits >> (5 * i)) & 31));
+    const uint64_t h = pair_key(src[e], dst[e]);
+    filter_insert(h, nblk, words);
+    filter_insert(labelled_key(h, elab[e]), nblk, words);
+  }
+}
+
+__global__ void k_hash(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                       const int32_t *__restrict__ elab, int64_t m, uint32_t nbkt,
+                       int4 *__restrict__ table, uint32_t *__restrict__ err) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = src[e], v = dst[e];
+    const unsigned long long key = ((unsigned long long)(uint32_t)v << 32) | (uint32_t)u;
+    uint32_t b = hash_bucket(pair_key(u, v), nbkt);
+    bool placed = false;
+    // at most every bucket once: the table has twice as many slots as arcs
+    for (uint32_t it = 0; it < nbkt && !placed; ++it) {
+      for (int s = 0; s < 2 && !placed; ++s) {
+        int4 *slot = table + 2 * (size_t)b + s;
+        const unsigned long long old =
+            atomicCAS(reinterpret_cast<unsigned long long *>(slot), ~0ull, key);
+        if (old == ~0ull) {
+          slot->z = elab[e];
+          placed = true;
+        }
+      }
+      b = b + 1 == nbkt ? 0 : b + 1;
+    }
+    if (!placed) atomicOr(err, kErrHash);
   }
 }
 
@@ -312,9 +346,12 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
   HM_CUDA_TRY(dmalloc(&g->vi, n));
   HM_CUDA_TRY(dmalloc(&g->off, n));
   HM_CUDA_TRY(dmalloc(&g->vdir, n));
-  g->afilt_nblk = (uint32_t)std::max<int64_t>(1, (m + 15) / 16);
+  g->afilt_nblk = (uint32_t)std::max<int64_t>(1, (m + 7) / 8);
   HM_CUDA_TRY(dmalloc(&g->afilt, 2 * (int64_t)g->afilt_nblk));
   HM_CUDA_TRY(cudaMemsetAsync(g->afilt, 0, 32 * (size_t)g->afilt_nblk, s));
+  g->ahash_nbkt = (uint32_t)std::max<int64_t>(1, m);
+  HM_CUDA_TRY(dmalloc(&g->ahash, 2 * (int64_t)g->ahash_nbkt));
+  HM_CUDA_TRY(cudaMemsetAsync(g->ahash, 0xff, 32 * (size_t)g->ahash_nbkt, s));
 
   const int nbits = bits_for(n);
   int be = 1, bv = 1;
@@ -329,8 +366,10 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
     if (st != HM_OK) return st;
     k_split<<<grid_for(m), kThreads, 0, s>>>(rows, m, n, 0, 1, g->src, g->out_adj, g->out_elab,
                                              out_off, err);
-    k_filter<<<grid_for(m), kThreads, 0, s>>>(g->src, g->out_adj, m, g->afilt_nblk,
+    k_filter<<<grid_for(m), kThreads, 0, s>>>(g->src, g->out_adj, g->out_elab, m, g->afilt_nblk,
                                               reinterpret_cast<uint32_t *>(g->afilt));
+    k_hash<<<grid_for(m), kThreads, 0, s>>>(g->src, g->out_adj, g->out_elab, m, g->ahash_nbkt,
+                                            g->ahash, err);
     st = build_groups(rows, tmp, m, n, 0, 1, d_vlab, out_off, nbits, be, xe, bv, xv, s, T,
                       &g->gout_adj, &g->gdir_out, &g->ndir_out, &oidx);
     if (st != HM_OK) return st;
@@ -356,15 +395,17 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
   HM_CUDA_TRY(cudaStreamSynchronize(s));
   HM_CUDA_TRY(cudaGetLastError());
   if (h_err & kErrDup) return HM_ERR_DUP_EDGE;
+  if (h_err & kErrHash) return HM_ERR_CUDA;  // cannot happen (twice as many slots as arcs)
   g->bytes = sizeof(int32_t) * 7 * (size_t)m + (sizeof(int4) * 2 + sizeof(int2)) * (size_t)n +
-             sizeof(int4) * (size_t)(g->ndir_out + g->ndir_in) + 32 * (size_t)g->afilt_nblk;
+             sizeof(int4) * (size_t)(g->ndir_out + g->ndir_in) + 32 * (size_t)g->afilt_nblk +
+             32 * (size_t)g->ahash_nbkt;
   return HM_OK;
 }
 
 void free_graph_arrays(hm_graph *g) {
   void *ptrs[] = {g->src,     g->out_adj,  g->out_elab, g->in_adj,   g->in_elab, g->vi,
                   g->off,     g->gout_adj, g->gin_adj,  g->gdir_out, g->gdir_in, g->vdir,
-                  g->afilt};
+                  g->afilt,   g->ahash};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }

@@ -9,8 +9,11 @@
 //   in_elab  int32[m]  label of each in-arc, parallel to in_adj
 //   vi       int4[n]   {vertex label, out-degree, in-degree, 0}
 //   off      int2[n]   {first out-arc, first in-arc}   (m < 2^31, so 32-bit offsets)
-//   afilt    uint4[2*B] arc-existence filter: B = ceil(m/16) blocks of 256 bits
-//                      (16 bits per arc; 32 MB for 16M arcs, so it stays in L2)
+//   afilt    uint4[2*B] arc filter: B = ceil(m/8) blocks of 256 bits holding two
+//                      keys per arc, (u, v) and (u, v, label), 16 bits per key
+//                      (64 MB for 16M arcs, within the 129 MB L2)
+//   ahash    int4[2*H] arc hash table: H = m buckets of two 16-byte slots
+//                      {u, v, label, 0} (32 bytes per arc, half the slots used)
 // A vertex's label and both degrees arrive in one 16-byte load; its list
 // offsets in a second one, fetched only when a list is actually searched.
 #pragma once
@@ -44,12 +47,15 @@ struct DevGraph {
   const int4 *gdir_out;  // {arc label, neighbour label, first, end} (relative to the list start)
   const int4 *gdir_in;
   const int4 *vdir;      // {first out entry, out entries, first in entry, in entries}
-  // split-block Bloom filter over the arcs (u, v), labels ignored: a "no" is
-  // exact, a "maybe" needs the search.  Searches over more than filt_min
-  // entries probe it first (filt_min < 0: never).
+  // split-block Bloom filter over the arcs, keyed by (u, v) and by (u, v,
+  // label): a "no" is exact, a "maybe" needs the search.  Searches over more
+  // than filt_min entries probe it first (filt_min < 0: never).
   const uint4 *afilt;
   uint32_t afilt_nblk;
   int32_t filt_min;
+  // exact arc lookup in one or two 32-byte reads, for what the filter lets through
+  const int4 *ahash;
+  uint32_t ahash_nbkt;
 };
 
 // One pairwise condition between the position being extended (p) and an
@@ -155,12 +161,15 @@ __device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32
 }
 
 // ---- arc filter -------------------------------------------------------------
-// Each arc (u, v) owns one 256-bit block (eight 32-bit words) chosen by a hash
-// of the pair and sets one bit in each word, at positions from a second hash.
-// Both hashes are the splitmix64 finalizer (Steele, Lea and Flood, "Fast
-// splittable pseudorandom number generators", OOPSLA 2014).  With 16 bits per
-// arc a pair that is not an arc passes all eight bits with probability about
-// 0.1 %; an arc always passes.
+// Every arc (u, v) with label l enters the filter under two keys: the pair
+// (u, v) -- "is there an arc at all", for induced non-arcs and the opposite-arc
+// test -- and the triple (u, v, l) -- "is there an arc with this label", for
+// the pattern's arcs.  A key owns one 256-bit block (eight 32-bit words)
+// chosen by a hash and sets one bit in each word, at positions from a second
+// hash.  The hashes are the splitmix64 finalizer (Steele, Lea and Flood, "Fast
+// splittable pseudorandom number generators", OOPSLA 2014).  At 16 bits per
+// key a key that was never inserted passes all eight bits with probability
+// about 0.1 %; an inserted key always passes.
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
@@ -172,18 +181,24 @@ struct FilterSlot {
   uint64_t bits;  // eight 5-bit positions, word i at bits [5i, 5i+5)
 };
 
-__host__ __device__ __forceinline__ FilterSlot filter_slot(int32_t u, int32_t v, uint32_t nblk) {
-  const uint64_t h = mix64(((uint64_t)(uint32_t)u << 32) | (uint32_t)v);
+__host__ __device__ __forceinline__ FilterSlot filter_slot_of(uint64_t h, uint32_t nblk) {
   FilterSlot f;
   f.blk = (uint32_t)(((h >> 32) * (uint64_t)nblk) >> 32);
   f.bits = mix64(h ^ 0x5851f42d4c957f2dull);
   return f;
 }
 
-// false: (u, v) is certainly not an arc.  true: it may be.
+__host__ __device__ __forceinline__ uint64_t pair_key(int32_t u, int32_t v) {
+  return mix64(((uint64_t)(uint32_t)u << 32) | (uint32_t)v);
+}
+
+__host__ __device__ __forceinline__ uint64_t labelled_key(uint64_t pair, int32_t lab) {
+  return mix64(pair + 0x632be59bd9b4e019ull * ((uint64_t)(uint32_t)lab + 1));
+}
+
 template <bool kCount>
-__device__ __forceinline__ bool arc_maybe(const DevGraph &G, int32_t u, int32_t v, uint64_t &bytes) {
-  const FilterSlot f = filter_slot(u, v, G.afilt_nblk);
+__device__ __forceinline__ bool filter_has(const DevGraph &G, uint64_t h, uint64_t &bytes) {
+  const FilterSlot f = filter_slot_of(h, G.afilt_nblk);
   const uint4 a = __ldg(G.afilt + 2 * (size_t)f.blk);
   const uint4 b = __ldg(G.afilt + 2 * (size_t)f.blk + 1);
   if (kCount) bytes += 32;
@@ -192,6 +207,52 @@ __device__ __forceinline__ bool arc_maybe(const DevGraph &G, int32_t u, int32_t 
                      (a.w >> ((x >> 15) & 31)) & (b.x >> ((x >> 20) & 31)) &
                      (b.y >> ((x >> 25) & 31)) & (b.z >> ((x >> 30) & 31)) & (b.w >> ((x >> 35) & 31));
   return t & 1u;
+}
+
+// false: there is certainly no arc u -> v.  true: there may be.
+template <bool kCount>
+__device__ __forceinline__ bool arc_maybe(const DevGraph &G, int32_t u, int32_t v, uint64_t &bytes) {
+  return filter_has<kCount>(G, pair_key(u, v), bytes);
+}
+
+// ---- arc hash table -----------------------------------------------------------
+// Open addressing over buckets of two 16-byte slots {u, v, label, 0}, one
+// 32-byte sector per bucket, with linear probing over buckets from the one the
+// pair's hash selects.  Slots fill in order and are never removed, so an empty
+// slot (u = -1) ends a probe sequence.  There are as many buckets as arcs
+// (half the slots used), so a lookup nearly always reads one sector.
+__host__ __device__ __forceinline__ uint32_t hash_bucket(uint64_t pair, uint32_t nbkt) {
+  return (uint32_t)(((pair & 0xffffffffull) * (uint64_t)nbkt) >> 32);
+}
+
+// Is u -> v an arc?  If so, *lab is its label.
+template <bool kCount>
+__device__ __forceinline__ bool arc_find(const DevGraph &G, int32_t u, int32_t v, int32_t *lab,
+                                         uint64_t &bytes) {
+  uint32_t b = hash_bucket(pair_key(u, v), G.ahash_nbkt);
+  for (uint32_t it = 0; it < G.ahash_nbkt; ++it) {
+    const int4 s0 = __ldg(G.ahash + 2 * (size_t)b);
+    const int4 s1 = __ldg(G.ahash + 2 * (size_t)b + 1);
+    if (kCount) bytes += 32;
+    if (s0.x == u && s0.y == v) {
+      *lab = s0.z;
+      return true;
+    }
+    if (s1.x == u && s1.y == v) {
+      *lab = s1.z;
+      return true;
+    }
+    if (s0.x < 0 || s1.x < 0) return false;
+    b = b + 1 == G.ahash_nbkt ? 0 : b + 1;
+  }
+  return false;
+}
+
+// false: there is certainly no arc u -> v with label lab.  true: there may be.
+template <bool kCount>
+__device__ __forceinline__ bool arc_maybe_l(const DevGraph &G, int32_t u, int32_t v, int32_t lab,
+                                            uint64_t &bytes) {
+  return filter_has<kCount>(G, labelled_key(pair_key(u, v), lab), bytes);
 }
 
 __device__ __forceinline__ int32_t search(const int32_t *__restrict__ a, int32_t lo, int32_t len,
@@ -234,6 +295,8 @@ struct hm_graph {
   int4 *gdir_out, *gdir_in, *vdir;
   uint4 *afilt;
   uint32_t afilt_nblk;
+  int4 *ahash;
+  uint32_t ahash_nbkt;
   int64_t ndir_out, ndir_in;
   size_t bytes;
   // multi-property graphs (hm_load_graph_props): the sorted distinct property
@@ -244,7 +307,7 @@ struct hm_graph {
   hm::DevGraph dev() const {
     return hm::DevGraph{n,        m,        src,     out_adj,  out_elab, in_adj,     in_elab,
                         vi,       off,      gout_adj, gin_adj, gdir_out, gdir_in,    vdir,
-                        afilt,    afilt_nblk, hm::filter_min()};
+                        afilt,    afilt_nblk, hm::filter_min(), ahash, ahash_nbkt};
   }
 };
 

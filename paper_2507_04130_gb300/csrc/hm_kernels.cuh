@@ -43,12 +43,6 @@
 
 #include "hm_internal.cuh"
 
-// 1: load a candidate's offsets together with its label/degree record;
-// 0: only after it passes the degree filter.
-#ifndef HM_EAGER_OFFSETS
-#define HM_EAGER_OFFSETS 0
-#endif
-
 namespace hm {
 
 void ensure_pool();
@@ -145,7 +139,8 @@ template <bool kC>
 __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t y, int32_t outdeg_x,
                                            int32_t indeg_y, int32_t *lab, uint64_t &ctr) {
   if (outdeg_x == 0 || indeg_y == 0) return false;
-  if (use_filter(G, min(outdeg_x, indeg_y)) && !arc_maybe<kC>(G, x, y, ctr)) return false;
+  if (use_filter(G, min(outdeg_x, indeg_y)))
+    return arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, lab, ctr);
   if (kC) ctr += 8;
   if (outdeg_x <= indeg_y) {
     const int32_t o = __ldg(&G.off[x].x);
@@ -185,6 +180,8 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
     // the arc opposite to the seeding one is (b -> a) in both seeding directions
     const int4 ib = P.seed_rev ? iu : iv;
     const int4 ia = P.seed_rev ? iv : iu;
+    if (P.back_req && use_filter(G, min(ib.y, ia.z)) && !arc_maybe_l<kC>(G, b, a, P.back_lab, ctr))
+      return false;
     int32_t lab = 0;
     bool found = arc_lookup<kC>(G, b, a, ib.y, ia.z, &lab, ctr);
     if (P.back_req && (!found || lab != P.back_lab)) return false;
@@ -274,11 +271,12 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
 template <bool kC>
 __device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, int2 oy,
                                         int32_t w, uint64_t &ctr) {
-  if (iy.y && (!use_filter(G, iy.y) || arc_maybe<kC>(G, y, w, ctr)) &&
-      search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0)
+  int32_t lab;
+  if (iy.y && (use_filter(G, iy.y) ? arc_maybe<kC>(G, y, w, ctr) && arc_find<kC>(G, y, w, &lab, ctr)
+                                   : search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0))
     return true;
-  return iy.z && (!use_filter(G, iy.z) || arc_maybe<kC>(G, w, y, ctr)) &&
-         search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0;
+  return iy.z && (use_filter(G, iy.z) ? arc_maybe<kC>(G, w, y, ctr) && arc_find<kC>(G, w, y, &lab, ctr)
+                                      : search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0);
 }
 
 // In batched launches (kB) each seed carries its pattern id; the threshold is
@@ -456,25 +454,15 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
     if (S.map[i] == c) return false;                        // injective
   if (root_mask && p == P.root_pos && !root_mask[c]) return false;
   const int nc = P.ncons[p];
-  // c's own degrees and offsets: needed for the degree filter (inner levels) and
-  // to search c's shorter list instead of a hub's
+  // c's own degrees: needed for the degree filter (inner levels) and to search
+  // c's shorter list instead of a hub's; its offsets only for such a search
   const bool need_c = !leaf || nc > 1;
   int4 vi = make_int4(0, 0, 0, 0);
-  int2 oc = make_int2(0, 0);
+  int2 oc = make_int2(-1, -1);
   if (need_c) {
-#if HM_EAGER_OFFSETS
-    // both records in flight together (the offsets are used by most searches)
-    if (kC) ctr += nc > 1 ? 32 : 16;
-    vi = __ldg(&G.vi[c]);
-    if (nc > 1) oc = __ldg(&G.off[c]);
-    if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
-#else
     if (kC) ctr += 16;
     vi = __ldg(&G.vi[c]);
     if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
-    if (kC && nc > 1) ctr += 16;
-    if (nc > 1) oc = __ldg(&G.off[c]);
-#endif
   }
   for (int j = 0; j < nc; ++j) {
     if (j == drive) continue;
@@ -482,15 +470,21 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
     const int q = cs.q;
     const int32_t fq = S.map[q];
     const bool fwd = cs.kind == kOut || cs.kind == kNotOut;   // arc f(q) -> c ?
+    const int32_t x = fwd ? fq : c, y = fwd ? c : fq;         // the arc in question, x -> y
     bool found;
+    int32_t lab;
     if (cs.kind <= kIn) {
       // positive: c in the (label, label) group of f(q), or f(q) in c's reverse list
       const int2 r = grp[P.gbase[p] + j];
       const int32_t rev_len = fwd ? vi.z : vi.y;
-      if (r.y == 0) return false;
-      if (use_filter(G, min(rev_len, r.y)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr))
-        return false;
-      if (rev_len < r.y) {
+      if (r.y == 0 || rev_len == 0) return false;
+      if (use_filter(G, min(rev_len, r.y))) {
+        found = arc_maybe_l<kC>(G, x, y, cs.lab, ctr) && arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab;
+      } else if (rev_len < r.y) {
+        if (oc.x < 0) {
+          if (kC) ctr += 8;
+          oc = __ldg(&G.off[c]);
+        }
         const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
                               : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
         if (kC && i >= 0) ctr += 4;
@@ -505,10 +499,15 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
       const int32_t lb = fwd ? vi.z : vi.y;
       if (la == 0 || lb == 0) continue;
-      if (use_filter(G, min(la, lb)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr)) continue;
-      if (la <= lb) {
+      if (use_filter(G, min(la, lb))) {
+        found = arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr);
+      } else if (la <= lb) {
         found = search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) >= 0;
       } else {
+        if (oc.x < 0) {
+          if (kC) ctr += 8;
+          oc = __ldg(&G.off[c]);
+        }
         found = search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) >= 0;
       }
       if (found) return false;
@@ -537,12 +536,14 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
   const int q = cs.q;
   const int32_t fq = S.map[q];
   const bool fwd = cs.kind == kOut || cs.kind == kNotOut;
+  const int32_t x = fwd ? fq : c, y = fwd ? c : fq;  // the arc in question, x -> y
+  int32_t lab;
   if (cs.kind <= kIn) {
     const int2 r = grp[P.gbase[p] + j];
     const int32_t rev_len = fwd ? vi.z : vi.y;
     if (r.y == 0 || rev_len == 0) return false;
-    if (use_filter(G, min(rev_len, r.y)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr))
-      return false;
+    if (use_filter(G, min(rev_len, r.y)))
+      return arc_maybe_l<kC>(G, x, y, cs.lab, ctr) && arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab;
     if (rev_len < r.y) {
       if (kC) ctr += 16;
       const int2 oc = __ldg(&G.off[c]);
@@ -557,7 +558,7 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
   const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
   const int32_t lb = fwd ? vi.z : vi.y;
   if (la == 0 || lb == 0) return true;
-  if (use_filter(G, min(la, lb)) && !arc_maybe<kC>(G, fwd ? fq : c, fwd ? c : fq, ctr)) return true;
+  if (use_filter(G, min(la, lb))) return !(arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr));
   if (la <= lb)
     return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
   if (kC) ctr += 16;
@@ -594,10 +595,10 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
   if (root_mask && p == P.root_pos && !root_mask[d]) return false;
   const int nc = P.ncons[p];
   if (nc <= 1) return true;
-  // first the arc filter, which needs only the two endpoints: most candidates
-  // fail a positive condition here, and most induced non-arcs are settled
-  uint64_t settled = 0;
   if (G.filt_min >= 0) {
+    // first the arc filter, which needs only the two endpoints: most candidates
+    // fail a positive condition here, and most induced non-arcs are settled
+    uint64_t settled = 0;
     for (int j = 0; j < nc; ++j) {
       if (j == drive) continue;
       const Cons cs = P.cons[p][j];
@@ -607,14 +608,49 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
       if (cs.kind <= kIn) {
         const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
         if (r.y == 0) return false;
-        if (use_filter(G, r.y) && !arc_maybe<kC>(G, fwd ? fq : d, fwd ? d : fq, ctr)) return false;
+        if (use_filter(G, r.y) && !arc_maybe_l<kC>(G, fwd ? fq : d, fwd ? d : fq, cs.lab, ctr))
+          return false;
       } else {
         const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[cs.q]) : (mine ? o.deg_in : S.deg_in[cs.q]);
         if (la == 0 || (use_filter(G, la) && !arc_maybe<kC>(G, fwd ? fq : d, fwd ? d : fq, ctr)))
           settled |= 1ull << j;
       }
     }
+    // then the exact answers: short lists of f(q) are searched, the rest
+    // looked up in the arc hash table -- d's own record is never needed
+    for (int j = 0; j < nc; ++j) {
+      if (j == drive || ((settled >> j) & 1)) continue;
+      const Cons cs = P.cons[p][j];
+      const int q = cs.q;
+      const bool mine = q == L;
+      const int32_t fq = mine ? o.c : S.map[q];
+      const bool fwd = cs.kind == kOut || cs.kind == kNotOut;
+      const int32_t x = fwd ? fq : d, y = fwd ? d : fq;
+      int32_t lab;
+      if (cs.kind <= kIn) {
+        const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
+        const bool found =
+            use_filter(G, r.y)
+                ? arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab
+                : search_c<kC>(fwd ? G.gout_adj : G.gin_adj,
+                               (fwd ? (mine ? o.off_out : S.off_out[q]) : (mine ? o.off_in : S.off_in[q])) + r.x,
+                               r.y, d, ctr) >= 0;
+        if (!found) return false;
+      } else {
+        const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[q]) : (mine ? o.deg_in : S.deg_in[q]);
+        const bool found =
+            use_filter(G, la)
+                ? arc_find<kC>(G, x, y, &lab, ctr)
+                : search_c<kC>(fwd ? G.out_adj : G.in_adj,
+                               fwd ? (mine ? o.off_out : S.off_out[q]) : (mine ? o.off_in : S.off_in[q]), la, d,
+                               ctr) >= 0;
+        if (found) return false;
+      }
+    }
+    return true;
   }
+  // without the filter: search the shorter of f(q)'s list and d's reverse list
+  const uint64_t settled = 0;
   if (kC) ctr += 32;
   const int4 vi = __ldg(&G.vi[d]);
   const int2 od = __ldg(&G.off[d]);

@@ -118,12 +118,12 @@ def test_tuning_rejects_bad_values(hm, bad):
 def test_tuning_defaults_roundtrip(hm):
     hm.set_tuning(extend_min_blocks=6, split_min=128, pair_mode=1, seeds_per_fetch=4, poll_every=8)
     assert hm.get_tuning() == dict(extend_min_blocks=6, split_min=128, pair_mode=1, seeds_per_fetch=4,
-                                   poll_every=8, leaf_flatten=1, arc_filter=4)
+                                   poll_every=8, leaf_flatten=1, arc_filter=1)
     hm.set_tuning(leaf_flatten=-1, arc_filter=-1)
     assert hm.get_tuning()["leaf_flatten"] == -1 and hm.get_tuning()["arc_filter"] == -1
     hm.set_tuning()
     assert hm.get_tuning() == dict(extend_min_blocks=5, split_min=64, pair_mode=0, seeds_per_fetch=1,
-                                   poll_every=128, leaf_flatten=1, arc_filter=4)
+                                   poll_every=128, leaf_flatten=1, arc_filter=1)
 
 
 def _bfs_order(k, src, dst):
