@@ -347,8 +347,9 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  * Launch knobs of the extension kernel (process-wide; read by calls that
  * start afterwards).  None of them changes any result, only speed.
  *   extend_min_blocks  resident 256-thread blocks per SM the kernel is
- *                      compiled for: 5 (default), 6 or 8 (fewer registers
- *                      per thread, more warps to hide load latency).
+ *                      compiled for: 4 (default, 64 registers per thread),
+ *                      5 or 6 (fewer registers, more warps to hide load
+ *                      latency, more register spills).
  *   split_min          a busy warp donates half of a candidate range to idle
  *                      warps only while the range holds at least this many
  *                      candidates (default 64, >= 2).
@@ -391,7 +392,7 @@ hm_status hm_get_tuning(hm_tuning *t);
 
 /* hm_autotune -- picks the knobs above for a workload: it times the batched
  * count (hm_count_batch) of the given patterns under candidate settings
- * (leaf flattening on/off, blocks per SM 5/6, split threshold 64/512, pair
+ * (leaf flattening on/off, blocks per SM 4/5, split threshold 64/512, pair
  * mode 0/1, poll interval 32/128/512, seeds per fetch 1/2, and the current
  * setting), best of two runs
  * each, until budget_ms of wall time is spent (0 = try all), installs the

@@ -10,7 +10,7 @@ std::atomic<uint64_t> g_budget_ms{120000};
 std::atomic<uint64_t> g_budget_chunks{0};
 std::atomic<int> g_timing{0};
 std::atomic<int> g_counters{0};
-std::atomic<int> g_min_blocks{5}, g_split_min{64}, g_pair_mode{0}, g_seeds_per_fetch{1};
+std::atomic<int> g_min_blocks{4}, g_split_min{64}, g_pair_mode{0}, g_seeds_per_fetch{1};
 std::atomic<int> g_poll_every{128};
 std::atomic<int> g_leaf_flatten{1};
 std::atomic<int> g_arc_filter{kDefaultFilterMin};
@@ -78,11 +78,11 @@ extern "C" hm_status hm_set_counters(int enabled) {
 
 extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   if (!t) return HM_ERR_ARG;
-  const int mb = t->extend_min_blocks ? t->extend_min_blocks : 5;
+  const int mb = t->extend_min_blocks ? t->extend_min_blocks : 4;
   const int sm = t->split_min ? t->split_min : 64;
   const int sp = t->seeds_per_fetch ? t->seeds_per_fetch : 1;
   const int pe = t->poll_every ? t->poll_every : 128;
-  if ((mb != 5 && mb != 6 && mb != 8) || sm < 2 || sp < 1 || sp > 1024 ||
+  if ((mb != 4 && mb != 5 && mb != 6) || sm < 2 || sp < 1 || sp > 1024 ||
       (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)) ||
       t->leaf_flatten < -1 || t->leaf_flatten > 1 || t->arc_filter < -1)
     return HM_ERR_ARG;

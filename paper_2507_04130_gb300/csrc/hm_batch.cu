@@ -438,7 +438,7 @@ extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *pat
   // reference run with the current knobs (also warms caches and the pool)
   hm_status st = hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, ref.data(), s);
   if (st != HM_OK) return st;
-  static const int32_t kMb[] = {5, 6};
+  static const int32_t kMb[] = {4, 5};
   static const int32_t kSplit[] = {64, 512};
   static const int32_t kPair[] = {0, 1};
   static const int32_t kPoll[] = {32, 128, 512};

@@ -1360,7 +1360,7 @@ using ExtendKernel = void (*)(DevGraph, Plan, ExtArgs);
 
 // Occupancy variants: resident 256-thread blocks per SM requested from the
 // compiler (it caps registers per thread accordingly).
-constexpr int kMinBlockChoices[3] = {5, 6, 8};
+constexpr int kMinBlockChoices[3] = {4, 5, 6};
 
 int min_blocks_slot(int min_blocks) {
   for (int i = 0; i < 3; ++i)
@@ -1371,9 +1371,9 @@ int min_blocks_slot(int min_blocks) {
 template <bool R, bool C, bool B>
 ExtendKernel extend_kernel_mb(int slot) {
   switch (slot) {
-    case 1: return k_extend<R, C, 6, B>;
-    case 2: return k_extend<R, C, 8, B>;
-    default: return k_extend<R, C, 5, B>;
+    case 1: return k_extend<R, C, 5, B>;
+    case 2: return k_extend<R, C, 6, B>;
+    default: return k_extend<R, C, 4, B>;
   }
 }
 

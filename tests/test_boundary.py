@@ -122,7 +122,7 @@ def test_tuning_defaults_roundtrip(hm):
     hm.set_tuning(leaf_flatten=-1, arc_filter=-1)
     assert hm.get_tuning()["leaf_flatten"] == -1 and hm.get_tuning()["arc_filter"] == -1
     hm.set_tuning()
-    assert hm.get_tuning() == dict(extend_min_blocks=5, split_min=64, pair_mode=0, seeds_per_fetch=1,
+    assert hm.get_tuning() == dict(extend_min_blocks=4, split_min=64, pair_mode=0, seeds_per_fetch=1,
                                    poll_every=128, leaf_flatten=1, arc_filter=1)
 
 

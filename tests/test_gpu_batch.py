@@ -115,7 +115,7 @@ def test_autotune_picks_valid_knobs_and_keeps_results(hm):
     ref = hm.count_batch(G, P, hm.INDUCED)
     try:
         best = hm.autotune(G, P, hm.INDUCED, budget_ms=3000)
-        assert best["extend_min_blocks"] in (5, 6, 8) and best["ms"] > 0
+        assert best["extend_min_blocks"] in (4, 5, 6) and best["ms"] > 0
         assert hm.get_tuning() == {k: v for k, v in best.items() if k != "ms"}
         assert hm.count_batch(G, P, hm.INDUCED) == ref
     finally:

@@ -385,7 +385,7 @@ def test_instrumented_kernels_agree_and_count_bytes(hm):
     assert st["bytes_extend"] > 0 and st["candidates"] > 0
 
 
-@pytest.mark.parametrize("knobs", [dict(extend_min_blocks=6), dict(extend_min_blocks=8),
+@pytest.mark.parametrize("knobs", [dict(extend_min_blocks=5), dict(extend_min_blocks=6),
                                    dict(pair_mode=1), dict(split_min=2, seeds_per_fetch=7),
                                    dict(pair_mode=1, split_min=2, poll_every=1),
                                    dict(poll_every=65536), dict(leaf_flatten=-1),
