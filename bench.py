@@ -51,6 +51,10 @@ def parse_args(argv=None):
                     help="skip the batched-vs-sequential and serving measurements")
     ap.add_argument("--ablation", action="store_true",
                     help="instead: the reordering ablation (Alg. 1 vs breadth-first order) on 60 ER graphs")
+    ap.add_argument("--report", action="store_true",
+                    help="instead: every workload (ER, R-MAT, connectome, batched, served) with mean and 95%% CI "
+                         "of repeated runs, per-kernel rates and the oracle on 1 and on all host cores")
+    ap.add_argument("--repeats", type=int, default=7, help="runs per figure in --report")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     return ap.parse_args(argv)
@@ -445,7 +449,7 @@ def measure_batched(hm, G, torch, reps=3):
 
 
 def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=3.0, max_queries=200,
-                    slots=4, max_batch=32):
+                    slots=4, max_batch=32, n_vlab=8, n_elab=4):
     """Open-loop Poisson arrivals of motif queries against the resident graph, through hm_server."""
     import threading
 
@@ -454,7 +458,7 @@ def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=3.0, max_quer
     out = []
     for rate in rates:
         n = int(min(max_queries, max(20, rate * seconds)))
-        arrivals = synth.config5_arrivals(rate, n, n_vlab=8, n_elab=4)
+        arrivals = synth.config5_arrivals(rate, n, n_vlab=n_vlab, n_elab=n_elab)
         srv = hm.Server(G, slots=slots, max_batch=max_batch)
         ids = [None] * n
         t0 = time.perf_counter()
@@ -468,11 +472,15 @@ def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=3.0, max_quer
 
         th = threading.Thread(target=producer)
         th.start()
-        lat, matches = [], 0
+        lat, matches, failed = [], 0, 0
         for i in range(n):
             while ids[i] is None:
                 time.sleep(0.0002)
-            r = srv.result(ids[i])
+            try:
+                r = srv.result(ids[i])
+            except hm.HMError:   # e.g. the work budget ran out for this query's batch
+                failed += 1
+                continue
             lat.append(r["latency_ms"])
             matches += r["count"]
         th.join()
@@ -480,16 +488,18 @@ def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=3.0, max_quer
         st = srv.stats()
         srv.close()
         lat.sort()
+        nl = max(len(lat), 1)
         out.append({
-            "rate_qps": rate, "queries": n, "p50_ms": round(statistics.median(lat), 3),
-            "p99_ms": round(lat[min(n - 1, int(round(0.99 * (n - 1))))], 3),
+            "rate_qps": rate, "queries": n, "failed": failed,
+            "p50_ms": round(statistics.median(lat), 3) if lat else None,
+            "p99_ms": round(lat[min(nl - 1, int(round(0.99 * (nl - 1))))], 3) if lat else None,
             "matches": int(matches), "matches_per_s": round(matches / wall, 1),
             "achieved_qps": round(n / wall, 1), "batches": st["batches"],
             "max_inflight_batches": st["max_inflight_batches"], "rows_dropped": st["rows_dropped"],
         })
     return {"workload": ("Poisson arrivals, k ~ U{3..7}, density U[0.4,1.0], labels uniform over the "
-                         "graph's label sets, mode Bernoulli(1/2), rows returned, resident R-MAT graph; "
-                         f"{slots} dispatcher slots, batches of up to {max_batch}"),
+                         f"graph's label sets ({n_vlab} vertex, {n_elab} arc), mode Bernoulli(1/2), rows returned, "
+                         f"resident graph; {slots} dispatcher slots, batches of up to {max_batch}"),
             "rates": out}
 
 
@@ -620,9 +630,177 @@ def run_ablation(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# report: all five workloads
+# ---------------------------------------------------------------------------
+
+def mean_ci(xs):
+    """Mean and the half-width of its 95 % confidence interval (Student t)."""
+    n = len(xs)
+    m = statistics.mean(xs)
+    if n < 2:
+        return m, 0.0
+    try:
+        from scipy.stats import t as student_t
+        q = float(student_t.ppf(0.975, n - 1))
+    except ImportError:
+        q = 1.96
+    return m, q * statistics.stdev(xs) / n ** 0.5
+
+
+def _fig(xs, nd=3):
+    m, h = mean_ci(xs)
+    return {"mean": round(m, nd), "ci95": round(h, nd), "runs": len(xs)}
+
+
+def _time_query(hm, G, P, mode, rows, reps, flush):
+    """Per-kernel CUDA-event times (library timers) of repeated single-query calls."""
+    import torch
+
+    tot, ext, edge, srt, c = [], [], [], [], 0
+    for _ in range(reps + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        if rows:
+            r = hm.enumerate_matches(G, P, mode)
+            c = int(r.shape[0])
+        else:
+            c = hm.count_matches(G, P, mode)
+        st = hm.last_stats()
+        tot.append(st["ms_edge_scan"] + st["ms_overlap"] + st["ms_extend"] + st["ms_sort"])
+        ext.append(st["ms_extend"])
+        edge.append(st["ms_edge_scan"] + st["ms_overlap"])
+        srt.append(st["ms_sort"])
+    hm.set_counters(True)
+    if rows:
+        hm.enumerate_matches(G, P, mode)
+    else:
+        hm.count_matches(G, P, mode)
+    st = hm.last_stats()
+    hm.set_counters(False)
+    ext, edge = ext[1:], edge[1:]
+    return c, {
+        "ms": _fig(tot[1:]), "ms_extend": _fig(ext), "ms_edge_scan": _fig(edge), "ms_sort": _fig(srt[1:]),
+        "k_extend_GBps": round(st["bytes_extend"] / (statistics.mean(ext) / 1e3) / 1e9, 1) if statistics.mean(ext) else None,
+        "k_edge_seed_GBps": round((st["bytes_edge_scan"] + st["bytes_overlap"]) / (statistics.mean(edge) / 1e3) / 1e9, 1)
+        if statistics.mean(edge) else None,
+    }
+
+
+def _oracle_rate(og, pats, modes, n, target_s, threads, seed=0):
+    """Oracle matches/s on a seeded root sample grown to about target_s seconds."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)
+    roots = min(n, 256)
+    while True:
+        mask = np.zeros(n, np.uint8)
+        mask[perm[:roots]] = 1
+        t0 = time.perf_counter()
+        tot = sum(og.match(p, m, rows=False, threads=threads, root_mask=mask)[0] for p, m in zip(pats, modes))
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or roots >= n:
+            return {"matches_per_s": round(tot / dt, 1), "threads": threads, "roots": roots, "of": n,
+                    "matches": int(tot), "seconds": round(dt, 2)}
+        roots = min(n, int(roots * max(2.0, min(16.0, 0.8 * target_s / max(dt, 1e-3)))))
+
+
+def run_report(args):
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    import paper_2507_04130_gb300 as hm
+
+    torch.cuda.set_device(0)
+    hm.set_timing(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    reps = max(2, args.repeats)
+    cores = os.cpu_count() or 1
+    out = {"report": "all workloads, GB300, one GPU; figures are mean and 95 % CI half-width over runs",
+           "host_cores": cores}
+
+    def oracle_pair(og, pats, modes, n, budget):
+        return {"1_thread": _oracle_rate(og, pats, modes, n, budget, 1),
+                "all_cores": _oracle_rate(og, pats, modes, n, budget, cores)}
+
+    # ER, directed 3-cycle, monomorphism, count + rows; and the unlabelled diagnostic
+    g = synth.config1_graph()
+    sp = synth.config1_pattern()
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    P = hm.Pattern.from_synth(sp)
+    c, t = _time_query(hm, G, P, hm.MONO, True, reps, flush)
+    gu = synth.Graph(g.n, g.src, g.dst, np.zeros(g.n, np.int32), np.zeros(g.m, np.int32))
+    Gu = hm.Graph.from_synth(gu)
+    spu = synth.Pattern(3, sp.src, sp.dst, np.zeros(3, np.int32), np.zeros(3, np.int32), "cycle3u")
+    cu, tu = _time_query(hm, Gu, hm.Pattern.from_synth(spu), hm.MONO, True, reps, flush)
+    ogu = oracle.OracleGraph.from_synth(gu)
+    out["er"] = {"graph": f"ER n={g.n} m={g.m}", "pattern": "3-cycle, vlab (0,1,2), elab 0, mono",
+                 "matches": c, "oracle_matches": og.match(sp, oracle.MONO, rows=False)[0], **t,
+                 "unlabelled": {"matches": cu, "oracle_matches": ogu.match(spu, oracle.MONO, rows=False)[0], **tu},
+                 "oracle": oracle_pair(ogu, [spu], [oracle.MONO], g.n, 2.0)}
+    G.close(); Gu.close(); og.close(); ogu.close()
+
+    # R-MAT scale 20, three induced motifs, count + rows
+    g = synth.cached("rmat", synth.config2_graph, scale=20)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    q = {}
+    for sp in synth.config2_patterns():
+        c, t = _time_query(hm, G, hm.Pattern.from_synth(sp), hm.INDUCED, True, reps, flush)
+        q[sp.name] = {"matches": c, **t, "matches_per_s": round(c / (t["ms"]["mean"] / 1e3), 1)}
+    out["rmat"] = {"graph": f"R-MAT scale 20, n={g.n} m={g.m}", "mode": "induced, count + rows", "queries": q,
+                   "oracle": oracle_pair(og, synth.config2_patterns(), [oracle.INDUCED] * 3, g.n, 6.0)}
+
+    # batched 256 patterns vs 256 sequential calls (count + rows)
+    pats = synth.config4_patterns()
+    PB = [hm.Pattern.from_synth(p) for p in pats]
+    counts = hm.count_batch(G, PB, hm.INDUCED)
+
+    def wall(fn):
+        xs = []
+        for _ in range(reps + 1):
+            flush.fill_(2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            xs.append((time.perf_counter() - t0) * 1e3)
+        return xs[1:]
+
+    tb = wall(lambda: hm.enumerate_batch(G, PB, hm.INDUCED, counts=hm.count_batch(G, PB, hm.INDUCED)))
+    ts = wall(lambda: [hm.enumerate_matches(G, p, hm.INDUCED) for p in PB])
+    out["batched"] = {"patterns": len(PB), "matches": int(sum(counts)), "batched_ms": _fig(tb),
+                      "sequential_ms": _fig(ts), "speedup": round(statistics.mean(ts) / statistics.mean(tb), 2)}
+    out["served_rmat"] = measure_serving(hm, G)
+    G.close(); og.close()
+
+    # connectome-shaped, five 5-vertex monomorphism patterns, count only; serving on it
+    g = synth.cached("conn", synth.config3_graph)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    q = {}
+    cpats = synth.config3_patterns()
+    for sp in cpats:
+        c, t = _time_query(hm, G, hm.Pattern.from_synth(sp), hm.MONO, False, reps, flush)
+        q[sp.name] = {"matches": c, **t}
+    out["connectome"] = {"graph": f"Chung-Lu n={g.n} m={g.m}", "mode": "monomorphism, count only", "queries": q,
+                         "oracle": oracle_pair(og, cpats, [oracle.MONO] * 5, g.n, 6.0)}
+    hm.set_budget(5_000, 0)   # a served batch that needs more than 5 s is answered with HM_ERR_BUDGET
+    out["served_connectome"] = measure_serving(hm, G, rates=(10, 100, 1000), max_queries=60, n_vlab=6, n_elab=3)
+    hm.set_budget()
+    G.close(); og.close()
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.ablation:
+    if args.report:
+        run_report(args)
+    elif args.ablation:
         run_ablation(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -161,14 +161,16 @@ __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t
 // ---------------------------------------------------------------------------
 // edge scan: vertex validator + edge validator (label, opposite arc, degrees)
 // ---------------------------------------------------------------------------
+// `fresh`: the previous arc of this thread had another source (consecutive
+// arcs of one source share its record; the instrumented count takes it once).
 template <bool kC>
 __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int32_t a, int32_t b,
                                           int32_t l, const uint8_t *root_mask, int2 *out,
-                                          uint64_t &ctr) {
+                                          uint64_t &ctr, bool fresh = true) {
   if (l != P.seed_lab) return false;                       // match(e1, e2)
   const int32_t u = P.seed_rev ? b : a;                     // image of position 0
   const int32_t v = P.seed_rev ? a : b;                     // image of position 1
-  if (kC) ctr += 16;
+  if (kC && (fresh || P.seed_rev)) ctr += 16;
   const int4 iu = __ldg(&G.vi[u]);                          // Alg. 2 on u
   if (iu.x != P.vlab[0] || iu.y < P.dout[0] || iu.z < P.din[0]) return false;
   if (kC) ctr += 16;
@@ -192,6 +194,13 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
   return true;
 }
 
+// Each thread takes four consecutive arcs (one int4 of each stream) per step
+// and already has the next step's three int4 loads in flight while it tests
+// the current ones.  Survivors are appended to a per-warp buffer in shared
+// memory (warp prefix sum) and flushed to the seed queue with one atomic per
+// 32 or more seeds, so no block-wide barrier is needed.
+constexpr int kSeedBuf = 160;  // flushed at >= 32; one step adds at most 128
+
 template <bool kC>
 __global__ void __launch_bounds__(kSeedThreads)
 k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
@@ -199,63 +208,79 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
             unsigned long long cap, unsigned long long *__restrict__ nseeds,
             unsigned long long *__restrict__ bytes, int64_t e_begin, int64_t e_end) {
   uint64_t ctr = 0;
-  __shared__ uint32_t s_warp[kSeedThreads / 32];
-  __shared__ unsigned long long s_base;
+  __shared__ int2 s_buf[kSeedThreads / 32][kSeedBuf];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int2 *buf = s_buf[warp];
+  int nbuf = 0;  // same in every lane of the warp
   // arcs [e_begin, e_end), e_begin a multiple of 4 so the int4 streams stay aligned
   const int64_t ngroups = (e_end - e_begin + 3) >> 2;
   const int64_t full_groups = (e_end - e_begin) >> 2;
   const int4 *src4 = reinterpret_cast<const int4 *>(G.src + e_begin);
   const int4 *dst4 = reinterpret_cast<const int4 *>(G.out_adj + e_begin);
   const int4 *lab4 = reinterpret_cast<const int4 *>(G.out_elab + e_begin);
-  for (int64_t g0 = (int64_t)blockIdx.x * kSeedThreads; g0 < ngroups;
-       g0 += (int64_t)gridDim.x * kSeedThreads) {
-    const int64_t gi = g0 + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kSeedThreads;
+  int4 na = make_int4(0, 0, 0, 0), nb = na, nl = na;
+  {
+    const int64_t g0 = (int64_t)blockIdx.x * kSeedThreads + threadIdx.x;
+    if (g0 < full_groups) {
+      na = __ldcs(src4 + g0);
+      nb = __ldcs(dst4 + g0);
+      nl = __ldcs(lab4 + g0);
+    }
+  }
+  for (int64_t base = (int64_t)blockIdx.x * kSeedThreads; base < ngroups; base += stride) {
+    const int64_t gi = base + threadIdx.x;
+    const int4 a = na, b = nb, l = nl;
+    if (gi + stride < full_groups) {  // next step's arcs
+      na = __ldcs(src4 + gi + stride);
+      nb = __ldcs(dst4 + gi + stride);
+      nl = __ldcs(lab4 + gi + stride);
+    }
     int2 s[4];
     bool ok[4] = {false, false, false, false};
     if (gi < full_groups) {
-      int4 a = __ldcs(src4 + gi), b = __ldcs(dst4 + gi), l = __ldcs(lab4 + gi);
       if (kC) ctr += 48;
       ok[0] = seed_test<kC>(G, P, a.x, b.x, l.x, root_mask, &s[0], ctr);
-      ok[1] = seed_test<kC>(G, P, a.y, b.y, l.y, root_mask, &s[1], ctr);
-      ok[2] = seed_test<kC>(G, P, a.z, b.z, l.z, root_mask, &s[2], ctr);
-      ok[3] = seed_test<kC>(G, P, a.w, b.w, l.w, root_mask, &s[3], ctr);
+      ok[1] = seed_test<kC>(G, P, a.y, b.y, l.y, root_mask, &s[1], ctr, a.y != a.x);
+      ok[2] = seed_test<kC>(G, P, a.z, b.z, l.z, root_mask, &s[2], ctr, a.z != a.y);
+      ok[3] = seed_test<kC>(G, P, a.w, b.w, l.w, root_mask, &s[3], ctr, a.w != a.z);
     } else if (gi < ngroups) {
       for (int j = 0; j < 4; ++j) {
-        int64_t e = e_begin + gi * 4 + j;
+        const int64_t e = e_begin + gi * 4 + j;
         if (kC && e < e_end) ctr += 12;
         if (e < e_end)
           ok[j] = seed_test<kC>(G, P, G.src[e], G.out_adj[e], G.out_elab[e], root_mask, &s[j], ctr);
       }
     }
-    uint32_t cnt = (uint32_t)ok[0] + ok[1] + ok[2] + ok[3];
+    const uint32_t cnt = (uint32_t)ok[0] + ok[1] + ok[2] + ok[3];
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(kFull, incl, o);
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += y;
     }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t acc = 0;
-      for (int w = 0; w < kSeedThreads / 32; ++w) {
-        uint32_t t = s_warp[w];
-        s_warp[w] = acc;
-        acc += t;
-      }
-      s_base = acc ? atomicAdd(nseeds, (unsigned long long)acc) : 0ull;
-    }
-    __syncthreads();
-    unsigned long long at = s_base + s_warp[warp] + (incl - cnt);
+    int at = nbuf + (int)(incl - cnt);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (ok[j]) {
-        if (at < cap) seeds[at] = s[j];
-        ++at;
-      }
+    for (int j = 0; j < 4; ++j)
+      if (ok[j]) buf[at++] = s[j];
+    nbuf += (int)__shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    if (nbuf >= 32) {
+      unsigned long long off = 0;
+      if (lane == 0) off = atomicAdd(nseeds, (unsigned long long)nbuf);
+      off = __shfl_sync(kFull, off, 0);
+      for (int i = lane; i < nbuf; i += 32)
+        if (off + i < cap) seeds[off + i] = buf[i];
+      nbuf = 0;
+      __syncwarp();
     }
-    __syncthreads();
+  }
+  if (nbuf) {
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(nseeds, (unsigned long long)nbuf);
+    off = __shfl_sync(kFull, off, 0);
+    for (int i = lane; i < nbuf; i += 32)
+      if (off + i < cap) seeds[off + i] = buf[i];
   }
   if (kC) {
     for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
