@@ -168,7 +168,7 @@ __device__ __forceinline__ void filter_insert(uint64_t h, uint32_t nblk, uint32_
   const FilterSlot f = filter_slot_of(h, nblk);
   uint32_t *w = words + 8 * (size_t)f.blk;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) atomicOr(w + i, 1u << ((f.bits >> (5 * i)) & 31));
+  for (int i = 0; i < 8; ++i) atomicOr(w + i, 1u << filter_bit(f.bits, i));
 }
 
 __global__ void k_filter(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,

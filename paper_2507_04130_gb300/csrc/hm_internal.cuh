@@ -165,11 +165,15 @@ __device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32
 // (u, v) -- "is there an arc at all", for induced non-arcs and the opposite-arc
 // test -- and the triple (u, v, l) -- "is there an arc with this label", for
 // the pattern's arcs.  A key owns one 256-bit block (eight 32-bit words)
-// chosen by a hash and sets one bit in each word, at positions from a second
-// hash.  The hashes are the splitmix64 finalizer (Steele, Lea and Flood, "Fast
-// splittable pseudorandom number generators", OOPSLA 2014).  At 16 bits per
-// key a key that was never inserted passes all eight bits with probability
-// about 0.1 %; an inserted key always passes.
+// chosen by the high half of its 64-bit hash and sets one bit in each word;
+// bit i sits at the top five bits of the low half times the i-th of eight odd
+// constants (a split-block Bloom filter).  The pair hash is the splitmix64
+// finalizer (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014); the triple's hash is the pair's xor a
+// label-dependent constant.  The eight constants are splitmix64 outputs from
+// seed 0x243F6A8885A308D3, made odd.  At 16 bits per key a key that was never
+// inserted passes all eight bits with probability about 0.1 %; an inserted key
+// always passes.
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
@@ -178,14 +182,20 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 struct FilterSlot {
   uint32_t blk;   // block index
-  uint64_t bits;  // eight 5-bit positions, word i at bits [5i, 5i+5)
+  uint32_t bits;  // low half of the key's hash; bit i is at filter_bit(bits, i)
 };
 
 __host__ __device__ __forceinline__ FilterSlot filter_slot_of(uint64_t h, uint32_t nblk) {
   FilterSlot f;
   f.blk = (uint32_t)(((h >> 32) * (uint64_t)nblk) >> 32);
-  f.bits = mix64(h ^ 0x5851f42d4c957f2dull);
+  f.bits = (uint32_t)h;
   return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t filter_bit(uint32_t bits, int i) {
+  const uint32_t salt[8] = {0x2cb0f69fu, 0x94170347u, 0xdd555951u, 0xdbafb151u,
+                            0x7e789b2fu, 0xf41e5637u, 0x0959d151u, 0xa97316f1u};
+  return (bits * salt[i]) >> 27;
 }
 
 __host__ __device__ __forceinline__ uint64_t pair_key(int32_t u, int32_t v) {
@@ -193,7 +203,7 @@ __host__ __device__ __forceinline__ uint64_t pair_key(int32_t u, int32_t v) {
 }
 
 __host__ __device__ __forceinline__ uint64_t labelled_key(uint64_t pair, int32_t lab) {
-  return mix64(pair + 0x632be59bd9b4e019ull * ((uint64_t)(uint32_t)lab + 1));
+  return pair ^ (0x632be59bd9b4e019ull * ((uint64_t)(uint32_t)lab + 1));
 }
 
 template <bool kCount>
@@ -202,10 +212,10 @@ __device__ __forceinline__ bool filter_has(const DevGraph &G, uint64_t h, uint64
   const uint4 a = __ldg(G.afilt + 2 * (size_t)f.blk);
   const uint4 b = __ldg(G.afilt + 2 * (size_t)f.blk + 1);
   if (kCount) bytes += 32;
-  const uint64_t x = f.bits;
-  const uint32_t t = (a.x >> (x & 31)) & (a.y >> ((x >> 5) & 31)) & (a.z >> ((x >> 10) & 31)) &
-                     (a.w >> ((x >> 15) & 31)) & (b.x >> ((x >> 20) & 31)) &
-                     (b.y >> ((x >> 25) & 31)) & (b.z >> ((x >> 30) & 31)) & (b.w >> ((x >> 35) & 31));
+  const uint32_t x = f.bits;
+  const uint32_t t = (a.x >> filter_bit(x, 0)) & (a.y >> filter_bit(x, 1)) & (a.z >> filter_bit(x, 2)) &
+                     (a.w >> filter_bit(x, 3)) & (b.x >> filter_bit(x, 4)) & (b.y >> filter_bit(x, 5)) &
+                     (b.z >> filter_bit(x, 6)) & (b.w >> filter_bit(x, 7));
   return t & 1u;
 }
 
