@@ -763,13 +763,20 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpSta
         const int4 *dir = cs.kind == kOut ? G.gdir_out : G.gdir_in;
         const int32_t first = cs.kind == kOut ? vd.x : vd.z, cnt = cs.kind == kOut ? vd.y : vd.w;
         r = make_int2(0, 0);
-        for (int32_t e = 0; e < cnt; ++e) {
-          const int4 ent = __ldg(dir + first + e);
-          if (kC) ctr += 16;
-          if (ent.x == cs.lab && ent.y == P.vlab[p]) {
-            r = make_int2(ent.z, ent.w - ent.z);
-            break;
-          }
+        // entries four at a time (independent loads, one round trip per four)
+        bool hit = false;
+        for (int32_t e0 = 0; e0 < cnt && !hit; e0 += 4) {
+          int4 ent[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            ent[t] = e0 + t < cnt ? __ldg(dir + first + e0 + t) : make_int4(0, 0, 0, 0);
+          if (kC) ctr += 16 * (uint64_t)min(4, cnt - e0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (!hit && e0 + t < cnt && ent[t].x == cs.lab && ent[t].y == P.vlab[p]) {
+              r = make_int2(ent[t].z, ent[t].w - ent[t].z);
+              hit = true;
+            }
         }
         o.own[cs.kind] = r;
         lo = (cs.kind == kOut ? of.x : of.y) + r.x;

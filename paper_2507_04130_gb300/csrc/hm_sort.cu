@@ -5,7 +5,8 @@
 // lexicographic order (original pattern-vertex columns) before they are
 // returned.  The key is the concatenation of the chosen columns, each
 // holding `bits` significant bits, most significant column first; it is
-// consumed 8 bits per pass.
+// consumed kDigitBits (10) bits per pass, so a 4-column key of 20-bit vertex
+// ids takes 8 passes.
 //
 // One pass = three kernels on a fixed grid of G blocks, block b owning the
 // contiguous row range [b*R, (b+1)*R):
@@ -25,7 +26,8 @@
 namespace hm {
 namespace {
 
-constexpr int kRadix = 256;
+constexpr int kDigitBits = 10;
+constexpr int kRadix = 1 << kDigitBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 4;
@@ -40,17 +42,17 @@ struct KeySpec {
   int shift;                 // bit position of this pass's digit within the whole key
 };
 
-// 8-bit digit starting at bit `shift` of the concatenated key of a row.
+// kDigitBits-bit digit starting at bit `shift` of the concatenated key of a row.
 __device__ __forceinline__ uint32_t digit_of(const int32_t *__restrict__ row, const KeySpec &ks) {
   uint32_t v = 0;
   int got = 0;
   int col_lo = 0;  // bit position of the current column's least significant bit
-  for (int i = ks.ncols - 1; i >= 0 && got < 8; --i) {
+  for (int i = ks.ncols - 1; i >= 0 && got < kDigitBits; --i) {
     const int b = ks.bits[i];
     const int want_lo = ks.shift + got;
     if (want_lo < col_lo + b) {
       const int r = want_lo - col_lo;
-      const int take = min(b - r, 8 - got);
+      const int take = min(b - r, kDigitBits - got);
       const uint32_t col = (uint32_t)__ldg(row + ks.cols[i]) ^ ks.xr[i];
       v |= ((col >> r) & ((take >= 32) ? 0xffffffffu : ((1u << take) - 1u))) << got;
       got += take;
@@ -338,7 +340,7 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
     ks.xr[i] = key_xor[i];
     total_bits += key_bits[i];
   }
-  const int passes = (total_bits + 7) / 8;
+  const int passes = (total_bits + kDigitBits - 1) / kDigitBits;
   int grid = (int)std::min<int64_t>((nrows + kTile - 1) / kTile, (int64_t)num_sms() * 4);
   int64_t per_block = (nrows + grid - 1) / grid;
   per_block = (per_block + kTile - 1) / kTile * kTile;
@@ -350,7 +352,7 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
   uint32_t *starts = hist + nhist, *sums = starts + nhist;
   int32_t *a = rows, *b = tmp;
   for (int p = 0; p < passes; ++p) {
-    ks.shift = p * 8;
+    ks.shift = p * kDigitBits;
     k_hist<<<grid, kSortThreads, 0, stream>>>(a, nrows, width, per_block, ks, hist, grid);
     // exclusive scan of the (digit, block) counts over many blocks
     k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, stream>>>(hist, nhist, sums);
