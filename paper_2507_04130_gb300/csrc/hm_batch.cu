@@ -396,7 +396,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   t_sort.stop();
   HM_CUDA_TRY(cudaGetLastError());
   int total_bits = bits_for(npat) + kmax * bits_for(g->n);
-  st.kernel_launches += 2 + 5 * ((total_bits + 7) / 8);
+  st.kernel_launches += 2 + radix_sort_launches(total_bits);
   if (timing) {
     HM_CUDA_TRY(cudaStreamSynchronize(s));
     st.ms_sort = t_sort.ms();

@@ -350,6 +350,9 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
                                const int *key_cols, const int *key_bits, const uint32_t *key_xor,
                                int nkey, cudaStream_t stream);
 
+// Kernel launches of one radix_sort_rows_cols call over keys of total_bits bits.
+int radix_sort_launches(int total_bits);
+
 // out[i] = in[0] + ... + in[i-1] for i in [0, n); values and total below 2^32.
 hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t stream);
 

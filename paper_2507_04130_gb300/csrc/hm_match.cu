@@ -173,7 +173,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     for (int i = 0; i < p->k; ++i) cols[i] = i;
     const int sort_cols = p->k;
     hm_status r = radix_sort_rows(out, tmp, (int64_t)h.count, p->k, cols, sort_cols, bits_for(g->n), s);
-    st.kernel_launches += 5 * ((sort_cols * bits_for(g->n) + 7) / 8);
+    st.kernel_launches += radix_sort_launches(sort_cols * bits_for(g->n));
     t.stop();
     if (r != HM_OK) return r;
     if (timing) {

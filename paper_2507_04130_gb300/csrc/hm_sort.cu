@@ -292,6 +292,10 @@ hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaS
 }
 
 
+int radix_sort_launches(int total_bits) {
+  return 5 * ((total_bits + kDigitBits - 1) / kDigitBits);  // hist, 3 scan kernels, scatter per pass
+}
+
 int bits_for(int64_t n) {
   int b = 1;
   while (b < 31 && (int64_t(1) << b) < n) ++b;
