@@ -375,6 +375,14 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      filter whose "no" is exact) and, on "maybe", its arc
  *                      hash table, instead of a binary search (default 1;
  *                      -1: always binary search).
+ *   share_seeds        1 (default): when no later pattern position has an arc
+ *                      to position 1, single-pattern monomorphism calls group
+ *                      the injected depth-2 states by their position-0 image,
+ *                      search the other positions once per image and choose
+ *                      position 1 last from the group's seeds (same result
+ *                      set, far less work when hubs carry many seeds); -1: one
+ *                      search per depth-2 state.  Induced calls always search
+ *                      per state.
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -385,6 +393,7 @@ typedef struct {
   int32_t poll_every;
   int32_t leaf_flatten;
   int32_t arc_filter;
+  int32_t share_seeds;
 } hm_tuning;
 
 hm_status hm_set_tuning(const hm_tuning *t);

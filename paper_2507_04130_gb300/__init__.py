@@ -406,10 +406,11 @@ def set_counters(enabled: bool):
 
 def set_tuning(extend_min_blocks: int = 0, split_min: int = 0, pair_mode: int = 0,
                seeds_per_fetch: int = 0, poll_every: int = 0, leaf_flatten: int = 0,
-               arc_filter: int = 0):
+               arc_filter: int = 0, share_seeds: int = 0):
     """Set the extension kernel's launch knobs (0 = default; results never change)."""
     t = binding.hm_tuning(int(extend_min_blocks), int(split_min), int(pair_mode),
-                          int(seeds_per_fetch), int(poll_every), int(leaf_flatten), int(arc_filter))
+                          int(seeds_per_fetch), int(poll_every), int(leaf_flatten), int(arc_filter),
+                          int(share_seeds))
     check(lib.hm_set_tuning(ctypes.byref(t)), "hm_set_tuning")
 
 

@@ -73,6 +73,7 @@ class hm_tuning(ctypes.Structure):
         ("poll_every", ctypes.c_int32),
         ("leaf_flatten", ctypes.c_int32),
         ("arc_filter", ctypes.c_int32),
+        ("share_seeds", ctypes.c_int32),
     ]
 
     def as_dict(self):

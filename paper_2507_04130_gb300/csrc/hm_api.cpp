@@ -14,6 +14,7 @@ std::atomic<int> g_min_blocks{4}, g_split_min{64}, g_pair_mode{0}, g_seeds_per_f
 std::atomic<int> g_poll_every{128};
 std::atomic<int> g_leaf_flatten{1};
 std::atomic<int> g_arc_filter{kDefaultFilterMin};
+std::atomic<int> g_share_seeds{1};
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -31,6 +32,7 @@ hm_tuning tuning() {
   t.poll_every = g_poll_every.load(std::memory_order_relaxed);
   t.leaf_flatten = g_leaf_flatten.load(std::memory_order_relaxed);
   t.arc_filter = g_arc_filter.load(std::memory_order_relaxed);
+  t.share_seeds = g_share_seeds.load(std::memory_order_relaxed);
   return t;
 }
 int32_t filter_min() { return g_arc_filter.load(std::memory_order_relaxed); }
@@ -84,7 +86,8 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   const int pe = t->poll_every ? t->poll_every : 128;
   if ((mb != 4 && mb != 5 && mb != 6) || sm < 2 || sp < 1 || sp > 1024 ||
       (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)) ||
-      t->leaf_flatten < -1 || t->leaf_flatten > 1 || t->arc_filter < -1)
+      t->leaf_flatten < -1 || t->leaf_flatten > 1 || t->arc_filter < -1 || t->share_seeds < -1 ||
+      t->share_seeds > 1)
     return HM_ERR_ARG;
   hm::g_min_blocks.store(mb);
   hm::g_split_min.store(sm);
@@ -93,6 +96,7 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   hm::g_poll_every.store(pe);
   hm::g_leaf_flatten.store(t->leaf_flatten < 0 ? -1 : 1);
   hm::g_arc_filter.store(t->arc_filter ? t->arc_filter : hm::kDefaultFilterMin);
+  hm::g_share_seeds.store(t->share_seeds < 0 ? -1 : 1);
   return HM_OK;
 }
 

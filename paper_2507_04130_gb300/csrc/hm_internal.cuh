@@ -94,7 +94,16 @@ struct Plan {
   int32_t npos[kMaxK];  // how many of them are kOut/kIn
   int32_t gbase[kMaxK]; // first group slot of position p (sum of npos before p)
   int32_t ngrp;         // group slots in total
+  // Shared position-0 states: when no later position has a pattern arc to
+  // position 1 (defer1), the seeds can be grouped by their position-0 image
+  // and position 1 chosen last, from the group's seed list; the induced
+  // non-arcs between position 1 and later positions are then checked for
+  // each chosen image (defer, with q the later position and the kind read as
+  // "f(q) -> v" for kNotOut, "v -> f(q)" for kNotIn).
+  int32_t defer1;
+  int32_t ndefer;
   Cons cons[kMaxK][kMaxCons];
+  Cons defer[kMaxCons];
 };
 
 // Budget / status words shared by all warps of one call.

@@ -56,12 +56,12 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint64_t kQueueCap = 1ull << 16;  // donated tasks in flight (power of two)
 
 struct Task {
-  int32_t depth;   // mapped positions (>= 2)
-  int32_t drive;   // driving condition index for position `depth`
-  uint32_t pmask;  // candidates allowed in the first chunk [lo, lo+32)
-  int32_t pid;     // pattern of the task (batched launches)
-  int32_t lo, hi;  // range of the driving list (absolute offsets)
-  int32_t pad[2];
+  int32_t depth;     // mapped positions (>= 2)
+  int32_t drive;     // driving condition index for position `depth`
+  uint32_t pmask;    // candidates allowed in the first chunk [lo, lo+32)
+  int32_t pid;       // pattern of the task (batched launches)
+  int32_t lo, hi;    // range of the driving list (absolute offsets)
+  int32_t vlo, vhi;  // shared position-0 states: the group's seeds [vlo, vhi)
   int32_t map[kMaxK];
 };
 static_assert(sizeof(Task) == 32 + 4 * kMaxK && sizeof(Task) % 16 == 0, "task layout");
@@ -79,6 +79,7 @@ struct Ctl {
   alignas(128) int32_t status;
   alignas(128) unsigned long long nseeds_raw; // arcs passing the edge scan
   unsigned long long nseeds;                  // after the overlap test
+  unsigned long long ngroups;                 // shared position-0 states
   unsigned long long count;
   unsigned long long rows_written;
   unsigned long long chunks;
@@ -118,6 +119,12 @@ struct ExtArgs {
   unsigned long long *row_cursor;     // rows each pattern has claimed
   int32_t grp_slots;                  // group slots per warp (max over the patterns)
   int32_t pad2;
+  // shared position-0 states (single-pattern launches with P.defer1): one
+  // int4 {u, first, end, 0} per distinct position-0 image instead of `seeds`,
+  // and the seeds sorted by (u, v), whose .y over [first, end) are the
+  // images position 1 may take
+  const int4 *groups;
+  const int2 *sorted_seeds;
 };
 
 using atomic_u64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
@@ -383,6 +390,7 @@ struct WarpState {
   int32_t base[kMaxK];      // start of the chunk whose survivors are pending
   uint32_t mask[kMaxK];     // pending survivors of that chunk
   int32_t drive[kMaxK];     // driving condition at each depth
+  int32_t vlo, vhi;         // shared position-0 states: the group's seeds
   Task stage;               // task being donated or received
 };
 // Each warp's WarpState is followed in shared memory by one int2 per positive
@@ -396,9 +404,11 @@ __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int 
   // three independent 16-byte loads spread over three lanes
   int4 vi = make_int4(0, 0, 0, 0), vd = make_int4(0, 0, 0, 0);
   int2 o = make_int2(0, 0);
-  if (lane == 0) vi = __ldg(&G.vi[c]);
-  if (lane == 1) o = __ldg(&G.off[c]);
-  if (lane == 2) vd = __ldg(&G.vdir[c]);
+  if (c >= 0) {  // c < 0: position 1 of a shared position-0 state, not yet chosen
+    if (lane == 0) vi = __ldg(&G.vi[c]);
+    if (lane == 1) o = __ldg(&G.off[c]);
+    if (lane == 2) vd = __ldg(&G.vdir[c]);
+  }
   const int32_t dout = __shfl_sync(kFull, vi.y, 0), din = __shfl_sync(kFull, vi.z, 0);
   const int32_t oo = __shfl_sync(kFull, o.x, 1), oi = __shfl_sync(kFull, o.y, 1);
   int4 d;
@@ -716,11 +726,113 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
   return true;
 }
 
+// ---- shared position-0 states: choosing position 1 last ---------------------
+//
+// With P.defer1 every seed (u, v) of one position-0 image u shares the search
+// over positions 2..k-1, which never looks at position 1 (no pattern arc
+// joins it to a later position).  A warp extends one image u with position 1
+// unset; at each complete assignment M of the other positions it chooses
+// position 1 among the group's seed images v: v must not be in M, and in
+// induced mode the non-arcs between position 1 and later positions (P.defer)
+// must hold.  Positions 0..nmapped-1 are in S.map (S.map[1] = -1); the last
+// one or two positions are given: mK at k-1 and, when nmapped == k-2, mL at k-2.
+
+// Is there an arc x -> y (any label)?
+template <bool kC>
+__device__ __forceinline__ bool arc_exists(const DevGraph &G, int32_t x, int32_t y, uint64_t &ctr) {
+  int32_t lab;
+  if (G.filt_min >= 0) return arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr);
+  if (kC) ctr += 32;
+  const int4 ix = __ldg(&G.vi[x]), iy = __ldg(&G.vi[y]);
+  return arc_lookup<kC>(G, x, y, ix.y, iy.z, &lab, ctr);
+}
+
+// Is x among the group's images sorted_seeds[lo, hi).y (ascending)?
+__device__ __forceinline__ bool group_has(const int2 *__restrict__ sv, int32_t lo, int32_t hi, int32_t x) {
+  while (lo < hi) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    const int32_t y = __ldg(&sv[mid].y);
+    if (y < x) lo = mid + 1;
+    else if (y > x) hi = mid;
+    else return true;
+  }
+  return false;
+}
+
+template <bool kRows, bool kC>
+__device__ void expand_position1(const DevGraph &G, const Plan &P, const WarpState &S, const ExtArgs &A,
+                                 bool ok, int nmapped, int32_t mL, int32_t mK, int lane,
+                                 unsigned long long &task_count, unsigned long long *row_cursor,
+                                 int32_t *row_base, unsigned long long row_cap, uint64_t &ctr) {
+  const int k = P.k;
+  const int32_t vlo = S.vlo, vhi = S.vhi;
+  if (!kRows && P.ndefer == 0) {
+    // monomorphism count: every image of the group not used by M
+    unsigned long long add = 0;
+    if (ok) {
+      int used = group_has(A.sorted_seeds, vlo, vhi, mK) ? 1 : 0;
+      if (nmapped == k - 2 && group_has(A.sorted_seeds, vlo, vhi, mL)) ++used;
+      for (int i = 0; i < nmapped; ++i)
+        if (i != 1 && group_has(A.sorted_seeds, vlo, vhi, S.map[i])) ++used;
+      add = (unsigned long long)(vhi - vlo - used);
+      if (kC) ctr += 8ull * (nmapped + 1);
+    }
+    for (int o = 16; o; o >>= 1) add += __shfl_xor_sync(kFull, add, o);
+    task_count += add;
+    return;
+  }
+  // every (match M of a lane with ok, image v of the group) pair, 32 pairs per step
+  const uint32_t okm = __ballot_sync(kFull, ok);
+  const int32_t nv = vhi - vlo;
+  const int64_t total = (int64_t)__popc(okm) * nv;
+  for (int64_t g0 = 0; g0 < total; g0 += 32) {
+    const int64_t g = g0 + lane;
+    const bool live = g < total;
+    const int j = live ? (int)(g / nv) : 0;         // which ok lane's M
+    const int32_t vi = live ? (int32_t)(g - (int64_t)j * nv) : 0;
+    const int src = (int)__fns(okm, 0, j + 1);       // lane of the (j+1)-th set bit
+    const int32_t cL = __shfl_sync(kFull, mL, src);
+    const int32_t cK = __shfl_sync(kFull, mK, src);
+    bool good = false;
+    int32_t v = -1;
+    if (live) {
+      v = __ldg(&A.sorted_seeds[vlo + vi].y);
+      if (kC) ctr += 8;
+      good = v != cK && (nmapped == k - 1 || v != cL);
+      for (int i = 0; i < nmapped && good; ++i)
+        if (S.map[i] == v) good = false;  // injective (S.map[1] = -1)
+      for (int jj = 0; jj < P.ndefer && good; ++jj) {
+        const Cons cs = P.defer[jj];
+        const int32_t fq = cs.q < nmapped ? S.map[cs.q] : (cs.q == k - 1 ? cK : cL);
+        const bool fwd = cs.kind == kNotOut;  // the forbidden arc is f(q) -> v
+        if (arc_exists<kC>(G, fwd ? fq : v, fwd ? v : fq, ctr)) good = false;
+      }
+    }
+    const uint32_t bal = __ballot_sync(kFull, good);
+    const int nm = __popc(bal);
+    task_count += nm;
+    if (kRows && nm) {
+      unsigned long long at = 0;
+      if (lane == 0) at = atomicAdd(row_cursor, (unsigned long long)nm);
+      at = __shfl_sync(kFull, at, 0);
+      if (good) {
+        const unsigned long long r = at + __popc(bal & lanemask_lt());
+        if (r < row_cap) {
+          if (kC) ctr += 4 * k;
+          int32_t *row = row_base + r * k;
+          for (int i = 0; i < k; ++i)
+            row[P.orig[i]] = i == 1 ? v : (i < nmapped ? S.map[i] : (i == k - 1 ? cK : cL));
+        }
+      }
+    }
+  }
+}
+
 // Runs the leaf of every survivor in `m` (bits over adj[base + lane]) that has
 // at most kFlatMax leaf candidates; returns the survivors left for the
 // ordinary descent.  Adds the matches to task_count and writes their rows.
-template <bool kRows, bool kC>
-__device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpState &S,
+template <bool kRows, bool kC, bool kShared>
+__device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpState &S, const ExtArgs &A,
                                  int2 *__restrict__ grp, int L, const int32_t *__restrict__ adj,
                                  int32_t base, uint32_t m, int lane, const uint8_t *root_mask,
                                  unsigned long long &task_count, unsigned long long *row_cursor,
@@ -840,6 +952,11 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpSta
       if (kC) ctr += 4;
       ok = check_leaf<kC>(G, P, S, grp, p, o_drv_j, d, oo, root_mask, ctr);
     }
+    if (kShared) {
+      expand_position1<kRows, kC>(G, P, S, A, ok, L, oo.c, d, lane, task_count, row_cursor, row_base,
+                                  row_cap, ctr);
+      continue;
+    }
     const uint32_t bal = __ballot_sync(kFull, ok);
     const int nm = __popc(bal);
     task_count += nm;
@@ -957,7 +1074,8 @@ __device__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0
     t.depth = l;
     t.drive = S.drive[l];
     t.pid = pid;
-    t.pad[0] = t.pad[1] = 0;
+    t.vlo = S.vlo;
+    t.vhi = S.vhi;
     for (int i = 0; i < kMaxK; ++i) t.map[i] = i < l ? S.map[i] : -1;
     if (kind == 0) {
       const int32_t mid = S.lo[l] + ((S.hi[l] - S.lo[l]) >> 1);
@@ -999,7 +1117,7 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int ngrp) {
   return (sizeof(WarpState) + sizeof(int2) * (size_t)ngrp + 15) / 16 * 16;
 }
 
-template <bool kRows, bool kC, int kMinBlocks, bool kBatch>
+template <bool kRows, bool kC, int kMinBlocks, bool kBatch, bool kShared = false>
 __global__ void __launch_bounds__(kExtThreads, kMinBlocks)
 k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
          const __grid_constant__ ExtArgs A) {
@@ -1031,11 +1149,23 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
       }
       const unsigned long long s = seed_at++;
       if (s < seed_end) {
-        const int2 uv = A.seeds[s];
-        if (kBatch) pid = A.seed_pid[s];
-        if (kC && lane == 0) ctr += kBatch ? 12 : 8;
-        set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
-        set_mapped<kC>(G, S, 1, uv.y, lane, ctr);
+        if (kShared) {
+          // a shared position-0 state: position 1 is chosen at the leaves
+          const int4 gr = A.groups[s];
+          if (kC && lane == 0) ctr += 16;
+          set_mapped<kC>(G, S, 0, gr.x, lane, ctr);
+          set_mapped<kC>(G, S, 1, -1, lane, ctr);
+          if (lane == 0) {
+            S.vlo = gr.y;
+            S.vhi = gr.z;
+          }
+        } else {
+          const int2 uv = A.seeds[s];
+          if (kBatch) pid = A.seed_pid[s];
+          if (kC && lane == 0) ctr += kBatch ? 12 : 8;
+          set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
+          set_mapped<kC>(G, S, 1, uv.y, lane, ctr);
+        }
         __syncwarp();
         got = 1;
       } else {
@@ -1119,6 +1249,10 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
       // install a donated task
       const int d = S.stage.depth;
       for (int i = 0; i < d; ++i) set_mapped<kC>(G, S, i, S.stage.map[i], lane, ctr);
+      if (lane == 0) {
+        S.vlo = S.stage.vlo;
+        S.vhi = S.stage.vhi;
+      }
       __syncwarp();
       setup_level<kC>(G, P, S, grp, d, lane, true, ctr);
       if (lane == 0) {
@@ -1248,6 +1382,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           atomicAdd(&A.ctl->level_chunks[level], 1ull);
           atomicAdd(&A.ctl->level_lanes[level], (unsigned long long)min((int32_t)take, hi - lo));
         }
+        if (kShared && leaf) {
+          // leaf of a shared position-0 state: choose position 1 for each survivor
+          expand_position1<kRows, kC>(G, P, S, A, ok, k - 1, -1, c, lane, task_count, row_cursor, row_base,
+                                      row_cap, ctr);
+          __syncwarp();
+          continue;
+        }
         if (leaf) {
           // leaf: every survivor is a match
           const int nm = __popc(m);
@@ -1271,7 +1412,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         }
         uint32_t pending = m;
         if (A.leaf_flatten && level == k - 2 && m)
-          pending = leaf_flatten<kRows, kC>(G, P, S, grp, level, adj, lo, m, lane, A.root_mask,
+          pending = leaf_flatten<kRows, kC, kShared>(G, P, S, A, grp, level, adj, lo, m, lane, A.root_mask,
                                             task_count, row_cursor, row_base, row_cap, A.ctl,
                                             my_chunks, ctr);
         if (lane == 0) {
@@ -1400,33 +1541,43 @@ int min_blocks_slot(int min_blocks) {
   return 0;
 }
 
-template <bool R, bool C, bool B>
+template <bool R, bool C, bool B, bool S>
 ExtendKernel extend_kernel_mb(int slot) {
   switch (slot) {
-    case 1: return k_extend<R, C, 5, B>;
-    case 2: return k_extend<R, C, 6, B>;
-    default: return k_extend<R, C, 4, B>;
+    case 1: return k_extend<R, C, 5, B, S>;
+    case 2: return k_extend<R, C, 6, B, S>;
+    default: return k_extend<R, C, 4, B, S>;
   }
 }
 
-template <bool B = false>
-ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0) {
+template <bool B, bool S>
+ExtendKernel extend_kernel_s(bool rows, bool counters, int slot) {
   if (rows)
-    return counters ? extend_kernel_mb<true, true, B>(slot) : extend_kernel_mb<true, false, B>(slot);
-  return counters ? extend_kernel_mb<false, true, B>(slot) : extend_kernel_mb<false, false, B>(slot);
+    return counters ? extend_kernel_mb<true, true, B, S>(slot) : extend_kernel_mb<true, false, B, S>(slot);
+  return counters ? extend_kernel_mb<false, true, B, S>(slot) : extend_kernel_mb<false, false, B, S>(slot);
+}
+
+// The extension kernel for a launch; `shared` (shared position-0 states)
+// exists for single-pattern launches only.
+template <bool B = false>
+ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0, bool shared = false) {
+  if constexpr (!B) {
+    if (shared) return extend_kernel_s<false, true>(rows, counters, slot);
+  }
+  return extend_kernel_s<B, false>(rows, counters, slot);
 }
 
 // Resident blocks of an extension kernel variant for a dynamic shared-memory size.
 template <bool B = false>
-int extend_grid(bool rows, bool counters, size_t smem, int slot = 0) {
-  static std::atomic<int> cache[3][4][64];  // zero-initialised (static storage)
+int extend_grid(bool rows, bool counters, size_t smem, int slot = 0, bool shared = false) {
+  static std::atomic<int> cache[3][8][64];  // zero-initialised (static storage)
   const int sm = (int)std::min<size_t>(smem / 1024, 63);
-  std::atomic<int> &c = cache[slot][(rows ? 2 : 0) + (counters ? 1 : 0)][sm];
+  std::atomic<int> &c = cache[slot][(shared ? 4 : 0) + (rows ? 2 : 0) + (counters ? 1 : 0)][sm];
   int v = c.load(std::memory_order_relaxed);
   if (!v) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, extend_kernel<B>(rows, counters, slot), kExtThreads, smem);
+        &per_sm, extend_kernel<B>(rows, counters, slot, shared), kExtThreads, smem);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       return 0;

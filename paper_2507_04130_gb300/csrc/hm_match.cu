@@ -12,6 +12,49 @@ namespace {
 
 enum class Want { kCount, kRows, kStates };
 
+// The plan for shared position-0 states: the induced non-arcs between
+// position 1 and later positions leave the per-position condition lists and
+// become P.defer, read from the chosen image v of position 1.
+Plan shared_plan(const Plan &P) {
+  Plan Q = P;
+  Q.ndefer = 0;
+  for (int p = 2; p < P.k; ++p) {
+    int c = 0;
+    for (int j = 0; j < P.ncons[p]; ++j) {
+      const Cons cs = P.cons[p][j];
+      if (cs.q == 1)  // only induced non-arcs can name position 1 here (defer1)
+        Q.defer[Q.ndefer++] = Cons{(int8_t)p, cs.kind == kNotOut ? kNotIn : kNotOut, 0, 0};
+      else
+        Q.cons[p][c++] = cs;
+    }
+    Q.ncons[p] = c;
+  }
+  return Q;
+}
+
+// Seeds sorted by (u, v): flag the first seed of each position-0 image.
+__global__ void k_seed_group_flags(const int2 *__restrict__ s, int64_t n, uint32_t *__restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = i < n && (i == 0 || s[i].x != s[i - 1].x) ? 1u : 0u;
+}
+
+// One int4 {u, first, end, 0} per group; idx is the exclusive scan of flag.
+__global__ void k_seed_groups(const int2 *__restrict__ s, int64_t n, const uint32_t *__restrict__ flag,
+                              const uint32_t *__restrict__ idx, int4 *__restrict__ groups,
+                              unsigned long long *__restrict__ ngroups) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t gi = idx[i] + flag[i] - 1;
+    int32_t *gw = reinterpret_cast<int32_t *>(groups + gi);
+    if (flag[i]) {
+      gw[0] = s[i].x;
+      gw[1] = (int32_t)i;
+      gw[3] = 0;
+    }
+    if (i + 1 == n || flag[i + 1]) gw[2] = (int32_t)(i + 1);
+    if (i + 1 == n) *ngroups = gi + 1;
+  }
+}
+
 // First arc of part `part` of `nparts` contiguous CSR ranges (multiple of 4; part == nparts gives m).
 int64_t part_start(int64_t m, int32_t part, int32_t nparts) {
   if (part >= nparts) return m;
@@ -98,6 +141,46 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     return HM_OK;
   }
 
+  // Shared position-0 states: group the seeds by their position-0 image.
+  // Monomorphism only: in induced mode the non-arcs between position 1 and
+  // the later positions prune each seed's search early, which measured faster
+  // than checking every (match, image) pair at the end.
+  const hm_tuning tu = tuning();
+  const bool share = p->k > 2 && plan.defer1 && !plan.induced && tu.share_seeds > 0;
+  const int4 *groups = nullptr;
+  Timer t_grp(s, timing && share);
+  if (share) {
+    unsigned long long ns = 0;
+    HM_CUDA_TRY(cudaMemcpyAsync(&ns, nseeds, sizeof(ns), cudaMemcpyDeviceToHost, s));
+    HM_CUDA_TRY(cudaStreamSynchronize(s));
+    int32_t *tmp;
+    uint32_t *flag, *idx;
+    int4 *gr;
+    HM_CUDA_TRY(sc.get((void **)&tmp, sizeof(int2) * (size_t)std::max<unsigned long long>(ns, 1)));
+    HM_CUDA_TRY(sc.get((void **)&flag, sizeof(uint32_t) * (size_t)(ns + 1)));
+    HM_CUDA_TRY(sc.get((void **)&idx, sizeof(uint32_t) * (size_t)(ns + 1)));
+    HM_CUDA_TRY(sc.get((void **)&gr, sizeof(int4) * (size_t)std::max<unsigned long long>(ns, 1)));
+    HM_CUDA_TRY(cudaMemsetAsync(&ctl->ngroups, 0, sizeof(unsigned long long), s));
+    if (ns > 0) {
+      const int cols[2] = {0, 1};
+      int2 *sd = const_cast<int2 *>(seeds);
+      hm_status r = radix_sort_rows(reinterpret_cast<int32_t *>(sd), tmp, (int64_t)ns, 2, cols, 2,
+                                    bits_for(g->n), s);
+      if (r != HM_OK) return r;
+      launches += radix_sort_launches(2 * bits_for(g->n));
+      const int gb = (int)std::min<unsigned long long>((ns + 256) / 256, (unsigned long long)sms * 8);
+      k_seed_group_flags<<<gb, 256, 0, s>>>(seeds, (int64_t)ns, flag);
+      r = exclusive_scan_u32(flag, idx, (int64_t)ns + 1, s);
+      if (r != HM_OK) return r;
+      k_seed_groups<<<gb, 256, 0, s>>>(seeds, (int64_t)ns, flag, idx, gr, &ctl->ngroups);
+      launches += 5;
+      HM_CUDA_TRY(cudaGetLastError());
+    }
+    groups = gr;
+    plan = shared_plan(plan);
+  }
+  t_grp.stop();
+
   // a4 + a5: state injection and extension
   const bool rows = want == Want::kRows;
   Timer t_ext(s, timing && p->k > 2);
@@ -115,6 +198,11 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     ExtArgs A{};
     A.seeds = seeds;
     A.nseeds = nseeds;
+    if (share) {
+      A.groups = groups;
+      A.sorted_seeds = seeds;
+      A.nseeds = &ctl->ngroups;
+    }
     A.qbuf = qbuf;
     A.qseq = qseq;
     A.ctl = ctl;
@@ -123,7 +211,6 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.root_mask = root_mask;
     A.budget_ns = budget_ms() * 1000000ull;
     A.max_chunks = budget_chunks();
-    const hm_tuning tu = tuning();
     A.split_min = tu.split_min;
     A.pair_mode = tu.pair_mode;
     A.seeds_per_fetch = tu.seeds_per_fetch;
@@ -131,11 +218,11 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
-    const int grid = extend_grid(rows, counters, smem, slot);
+    const int grid = extend_grid(rows, counters, smem, slot, share);
     if (grid <= 0) return HM_ERR_CUDA;
     st.extend_grid = grid;
     st.extend_block = kExtThreads;
-    extend_kernel(rows, counters, slot)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    extend_kernel(rows, counters, slot, share)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
     ++launches;
     t_ext.stop();
     HM_CUDA_TRY(cudaGetLastError());
@@ -144,7 +231,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   HM_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   HM_CUDA_TRY(cudaStreamSynchronize(s));
   st.ms_edge_scan = t_edge.ms();
-  st.ms_overlap = t_ov.ms();
+  st.ms_overlap = t_ov.ms() + t_grp.ms();
   st.ms_extend = t_ext.ms();
   st.seeds_scanned = (uint64_t)(e_end - e_begin);
   st.states_injected = plan.ov_need > 0 ? h.nseeds : h.nseeds_raw;

@@ -130,6 +130,10 @@ void build_plan(const PatternGraph &P, const int32_t *order, int induced, hm::Pl
   for (int w = 2; w < k; ++w)
     if ((A[0][w] || A[w][0]) && (A[1][w] || A[w][1])) ++ov;
   pl.ov_need = ov;
+  // position 1 has no pattern arc to any later position: its image can be chosen last
+  pl.defer1 = k >= 3;
+  for (int p = 2; p < k; ++p)
+    if (A[1][p] || A[p][1]) pl.defer1 = 0;
   int slots = 0;
   for (int p = 2; p < k; ++p) {
     int c = 0;

@@ -426,3 +426,93 @@ def test_results_do_not_depend_on_the_order(hm):
             a = hm.enumerate_matches(G, P1, mode).cpu().numpy()
             b = hm.enumerate_matches(G, P2, mode).cpu().numpy()
             np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# shared position-0 states (position 1 chosen last)
+# ---------------------------------------------------------------------------
+
+def _position1_is_pendant(hm, sp):
+    """Does the vertex at position 1 of Alg. 1's order touch only the vertex at position 0?"""
+    order = hm.Pattern.from_synth(sp).order
+    v0, v1 = order[0], order[1]
+    nb = {int(b) for a, b in zip(sp.src, sp.dst) if a == v1} | {int(a) for a, b in zip(sp.src, sp.dst) if b == v1}
+    return nb == {v0}
+
+
+def _pendant_patterns(hm, rng, count, n_vlab, n_elab):
+    out = []
+    for _ in range(20000):
+        k = int(rng.integers(3, 7))
+        sp = synth.random_pattern(rng, k, float(rng.uniform(0.15, 0.6)), n_vlab=n_vlab, n_elab=n_elab,
+                                  name=f"pend{len(out)}")
+        if _position1_is_pendant(hm, sp):
+            out.append(sp)
+            if len(out) == count:
+                break
+    assert len(out) == count
+    return out
+
+
+def test_ffl_out_has_a_pendant_position_1(hm):
+    ffl = synth.config2_patterns()[0]
+    assert ffl.name == "ffl_out" and _position1_is_pendant(hm, ffl)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_shared_position0_states_equal_the_oracle(hm, seed):
+    rng = np.random.default_rng(300 + seed)
+    g = synth.small_random_graph(60, 0.2, 2, 2, seed=seed, recip=0.4, hub=True)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    for sp in _pendant_patterns(hm, rng, 6, 2, 2):
+        for mode in MODES:
+            want_c, want_r = og.match(sp, mode)
+            for share in (1, -1):
+                hm.set_tuning(share_seeds=share)
+                try:
+                    P = hm.Pattern.from_synth(sp)
+                    assert hm.count_matches(G, P, mode) == want_c, (sp.name, mode, share)
+                    np.testing.assert_array_equal(hm.enumerate_matches(G, P, mode).cpu().numpy(), want_r)
+                finally:
+                    hm.set_tuning()
+
+
+@pytest.mark.parametrize("knobs", [dict(arc_filter=-1), dict(leaf_flatten=-1), dict(pair_mode=1, split_min=2),
+                                   dict(split_min=2, poll_every=1)])
+def test_shared_position0_states_with_other_knobs(hm, knobs):
+    g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
+    g = synth.Graph(g0.n, g0.src, g0.dst, (g0.vlab % 2).astype(np.int32), g0.elab % 2)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    pats = _pendant_patterns(hm, np.random.default_rng(31), 4, 2, 2)
+    hm.set_tuning(**knobs)
+    try:
+        for sp in pats:
+            _check(hm, G, og, sp, oracle.INDUCED)
+            _check(hm, G, og, sp, oracle.MONO, rows=False)
+    finally:
+        hm.set_tuning()
+
+
+def test_shared_position0_states_rooted_and_parts(hm):
+    g = synth.config2_graph(scale=11)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    ffl = synth.config2_patterns()[0]
+    P = hm.Pattern.from_synth(ffl)
+    rng = np.random.default_rng(8)
+    for mode in MODES:
+        total = hm.count_matches(G, P, mode)
+        assert total == og.match(ffl, mode, rows=False)[0]
+        part = rng.integers(0, 3, g.n)
+        for root in range(ffl.k):
+            s = 0
+            for i in range(3):
+                mask = (part == i).astype(np.uint8)
+                c = hm.count_matches_rooted(G, P, mode, root, mask)
+                if root == 0:
+                    assert c == og.match(ffl, mode, rows=False, root_mask=mask)[0]
+                s += c
+            assert s == total
+        assert sum(hm.count_matches_part(G, P, mode, i, 3) for i in range(3)) == total
