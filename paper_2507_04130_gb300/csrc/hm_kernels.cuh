@@ -201,14 +201,16 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
   return true;
 }
 
-// Each warp scans one contiguous span of the arcs, 128 per step: each thread
-// takes four consecutive arcs (one int4 of each stream) and already has the
-// next step's three int4 loads in flight while it tests the current ones.
-// Survivors are appended to a per-warp buffer in shared memory (warp prefix
-// sum) and flushed to the seed queue with one atomic per 32 or more seeds, so
-// no block-wide barrier is needed, and seeds next to each other in the queue
-// come from nearby arcs (mostly the same source), which keeps the extension
-// kernel's concurrent warps on the same lists.
+// Each block scans one contiguous span of the arcs, 1024 per step (128 per
+// warp): each thread takes four consecutive arcs (one int4 of each stream) and
+// already has the next step's three int4 loads in flight while it tests the
+// current ones.  Survivors are appended to a per-warp buffer in shared memory
+// (warp prefix sum) and flushed to the seed queue with one atomic per 32 or
+// more seeds, so no block-wide barrier is needed, and seeds next to each other
+// in the queue come from nearby arcs (mostly the same source), which keeps the
+// extension kernel's concurrent warps on the same lists.  (One span per warp
+// kept the seeds closer still but streamed 9,728 separate regions and was
+// 1.7x slower on the 150M-arc graph.)
 constexpr int kSeedBuf = 160;  // flushed at >= 32; one step adds at most 128
 
 template <bool kC>
@@ -228,26 +230,25 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
   const int4 *src4 = reinterpret_cast<const int4 *>(G.src + e_begin);
   const int4 *dst4 = reinterpret_cast<const int4 *>(G.out_adj + e_begin);
   const int4 *lab4 = reinterpret_cast<const int4 *>(G.out_elab + e_begin);
-  const int64_t nwarps = (int64_t)gridDim.x * (kSeedThreads / 32);
-  const int64_t wid = (int64_t)blockIdx.x * (kSeedThreads / 32) + warp;
-  const int64_t span = ((ngroups + nwarps - 1) / nwarps + 31) / 32 * 32;  // groups per warp
-  const int64_t g_begin = wid * span, g_end = min(ngroups, g_begin + span);
+  const int64_t span = ((ngroups + gridDim.x - 1) / gridDim.x + kSeedThreads - 1) / kSeedThreads *
+                       kSeedThreads;  // groups per block
+  const int64_t g_begin = (int64_t)blockIdx.x * span, g_end = min(ngroups, g_begin + span);
   int4 na = make_int4(0, 0, 0, 0), nb = na, nl = na;
   {
-    const int64_t g0 = g_begin + lane;
+    const int64_t g0 = g_begin + threadIdx.x;
     if (g0 < g_end && g0 < full_groups) {
       na = __ldcs(src4 + g0);
       nb = __ldcs(dst4 + g0);
       nl = __ldcs(lab4 + g0);
     }
   }
-  for (int64_t base = g_begin; base < g_end; base += 32) {
-    const int64_t gi = base + lane;
+  for (int64_t base = g_begin; base < g_end; base += kSeedThreads) {
+    const int64_t gi = base + threadIdx.x;
     const int4 a = na, b = nb, l = nl;
-    if (gi + 32 < g_end && gi + 32 < full_groups) {  // next step's arcs
-      na = __ldcs(src4 + gi + 32);
-      nb = __ldcs(dst4 + gi + 32);
-      nl = __ldcs(lab4 + gi + 32);
+    if (gi + kSeedThreads < g_end && gi + kSeedThreads < full_groups) {  // next step's arcs
+      na = __ldcs(src4 + gi + kSeedThreads);
+      nb = __ldcs(dst4 + gi + kSeedThreads);
+      nl = __ldcs(lab4 + gi + kSeedThreads);
     }
     int2 s[4];
     bool ok[4] = {false, false, false, false};
