@@ -114,38 +114,13 @@ enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 
-// Lists of at most this many entries are compared with independent loads (one
-// round trip to the cache) instead of being halved one dependent probe at a
-// time; 0 = plain binary search to the end.
-#ifndef HM_SCAN_TAIL
-#define HM_SCAN_TAIL 0
-#endif
-constexpr int kScanTail = HM_SCAN_TAIL;
-
 // Is x in the sorted list a[lo, lo+len)?  Returns its index or -1.  Offsets are
-// 32-bit (the loader caps m below 2^31).  Halves the range while it is longer
-// than kScanTail, then compares the rest at once.
+// 32-bit (the loader caps m below 2^31).  kCount adds the bytes read to `bytes`.
 template <bool kCount>
 __device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32_t lo, int32_t len,
                                             int32_t x, uint64_t &bytes) {
-  if constexpr (kScanTail == 0) {
-    const int32_t end = lo + len;
-    while (len > 0) {
-      const int32_t half = len >> 1;
-      const int32_t v = __ldg(a + lo + half);
-      if (kCount) bytes += 4;
-      if (v < x) {
-        lo += half + 1;
-        len -= half + 1;
-      } else {
-        len = half;
-      }
-    }
-    if (lo >= end) return -1;
-    if (kCount) bytes += 4;
-    return __ldg(a + lo) == x ? lo : -1;
-  } else {
-  while (len > kScanTail) {
+  const int32_t end = lo + len;
+  while (len > 0) {
     const int32_t half = len >> 1;
     const int32_t v = __ldg(a + lo + half);
     if (kCount) bytes += 4;
@@ -153,20 +128,12 @@ __device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32
       lo += half + 1;
       len -= half + 1;
     } else {
-      len = half + 1;  // keep a[lo + half] (it may equal x)
+      len = half;
     }
   }
-  constexpr int kT = kScanTail > 0 ? kScanTail : 1;
-  int32_t v[kT];
-#pragma unroll
-  for (int i = 0; i < kT; ++i) v[i] = i < len ? __ldg(a + lo + i) : 0;
-  if (kCount) bytes += 4 * (uint64_t)len;
-  int32_t hit = -1;
-#pragma unroll
-  for (int i = kT - 1; i >= 0; --i)
-    if (i < len && v[i] == x) hit = lo + i;
-  return hit;
-  }
+  if (lo >= end) return -1;
+  if (kCount) bytes += 4;
+  return __ldg(a + lo) == x ? lo : -1;
 }
 
 // ---- arc filter -------------------------------------------------------------
@@ -272,12 +239,6 @@ template <bool kCount>
 __device__ __forceinline__ bool arc_maybe_l(const DevGraph &G, int32_t u, int32_t v, int32_t lab,
                                             uint64_t &bytes) {
   return filter_has<kCount>(G, labelled_key(pair_key(u, v), lab), bytes);
-}
-
-__device__ __forceinline__ int32_t search(const int32_t *__restrict__ a, int32_t lo, int32_t len,
-                                          int32_t x) {
-  uint64_t unused = 0;
-  return search_c<false>(a, lo, len, x, unused);
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
