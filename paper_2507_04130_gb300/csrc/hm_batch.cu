@@ -444,14 +444,16 @@ extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *pat
   static const int32_t kPoll[] = {32, 128, 512};
   static const int32_t kFetch[] = {1, 2};
   static const int32_t kFlat[] = {1, -1};
+  static const int32_t kFilter[] = {1, -1};  // membership tests: filter + hash table, or binary search
   std::vector<hm_tuning> cands;
   cands.push_back(before);
   for (int32_t fl : kFlat)
-    for (int32_t mb : kMb)
-      for (int32_t sp : kSplit)
-        for (int32_t pm : kPair)
-          for (int32_t po : kPoll)
-            for (int32_t fe : kFetch) cands.push_back(hm_tuning{mb, sp, pm, fe, po, fl});
+    for (int32_t af : kFilter)
+      for (int32_t mb : kMb)
+        for (int32_t sp : kSplit)
+          for (int32_t pm : kPair)
+            for (int32_t po : kPoll)
+              for (int32_t fe : kFetch) cands.push_back(hm_tuning{mb, sp, pm, fe, po, fl, af, before.share_seeds});
   const auto t_start = std::chrono::steady_clock::now();
   double best_t = 1e30;
   hm_tuning pick = before;
