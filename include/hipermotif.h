@@ -425,7 +425,9 @@ typedef struct {
   uint64_t chunks;          /* 32-candidate chunks examined                 */
   uint64_t matches;         /* the count of the call                        */
   float ms_edge_scan;       /* edge scan + validators                       */
-  float ms_overlap;         /* neighbour-overlap part of the edge validator  */
+  float ms_overlap;         /* neighbour-overlap part of the edge validator,
+                             * plus the seed grouping of shared position-0
+                             * states (share_seeds)                         */
   float ms_extend;          /* persistent extension kernel                  */
   float ms_sort;            /* row sort (enumerate only)                    */
   int32_t extend_grid;      /* blocks of the extension launch               */
