@@ -400,6 +400,12 @@ struct WarpState {
   uint32_t mask[kMaxK];     // pending survivors of that chunk
   int32_t drive[kMaxK];     // driving condition at each depth
   int32_t vlo, vhi;         // shared position-0 states: the group's seeds
+  // control state touched once per task or per 64 chunks (kept here, not in
+  // registers): the call's deadline, the seed count, this warp's claimed
+  // seeds [seed_at, seed_end), its match count and, for lane 0, the chunk
+  // count already reported and the last polled status and request words
+  unsigned long long deadline, nseeds, seed_at, seed_end, my_count, chunks_flushed;
+  int32_t requests_seen, status_seen;
   Task stage;               // task being donated or received
 };
 // Each warp's WarpState is followed in shared memory by one int2 per positive
@@ -1136,12 +1142,17 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
   const size_t stride = warp_smem_bytes(kBatch ? A.grp_slots : P0.ngrp);
   WarpState &S = *reinterpret_cast<WarpState *>(s_raw + (threadIdx.x >> 5) * stride);
   int2 *grp = reinterpret_cast<int2 *>(s_raw + (threadIdx.x >> 5) * stride + sizeof(WarpState));
-  const unsigned long long deadline = globaltimer_ns() + A.budget_ns;
-  const unsigned long long nseeds = *A.nseeds;
-  unsigned long long my_count = 0, my_chunks = 0;
-  unsigned long long chunks_flushed = 0, next_check = 64, next_poll = A.poll_mask + 1ull;
-  unsigned long long seed_at = 0, seed_end = 0;  // this warp's claimed seeds
-  int32_t requests_seen = 0, status_seen = kStatOk;  // lane 0: values from the previous poll
+  if (lane == 0) {
+    S.deadline = globaltimer_ns() + A.budget_ns;
+    S.nseeds = *A.nseeds;
+    S.seed_at = S.seed_end = 0;
+    S.my_count = 0;
+    S.chunks_flushed = 0;
+    S.requests_seen = 0;
+    S.status_seen = kStatOk;
+  }
+  __syncwarp();
+  unsigned long long my_chunks = 0, next_check = 64, next_poll = A.poll_mask + 1ull;
   bool seeds_done = false, stop = false;
   if (lane == 0) atomicAdd(&A.ctl->active, 1);
 
@@ -1150,13 +1161,20 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
     int got = 0;  // 1 seed, 2 donated
     int32_t pid = 0;
     if (!seeds_done) {
+      unsigned long long seed_at = S.seed_at, seed_end = S.seed_end;
       if (seed_at >= seed_end) {
         unsigned long long s0 = 0;
         if (lane == 0) s0 = atomicAdd(&A.ctl->seed_next, (unsigned long long)A.seeds_per_fetch);
         seed_at = __shfl_sync(kFull, s0, 0);
-        seed_end = min(seed_at + (unsigned long long)A.seeds_per_fetch, nseeds);
+        seed_end = min(seed_at + (unsigned long long)A.seeds_per_fetch, S.nseeds);
       }
-      const unsigned long long s = seed_at++;
+      const unsigned long long s = seed_at;
+      __syncwarp();
+      if (lane == 0) {
+        S.seed_at = seed_at + 1;
+        S.seed_end = seed_end;
+      }
+      __syncwarp();
       if (s < seed_end) {
         if (kShared) {
           // a shared position-0 state: position 1 is chosen at the leaves
@@ -1194,7 +1212,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         int quit = 0;
         if (lane == 0) {
           if (ld_volatile(&A.ctl->status) != kStatOk) quit = 1;
-          else if (globaltimer_ns() > deadline) {
+          else if (globaltimer_ns() > S.deadline) {
             atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
             quit = 1;
           } else {
@@ -1295,12 +1313,12 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           next_check = my_chunks + 64;
           int halt = 0;
           if (lane == 0) {
-            const unsigned long long add = my_chunks - chunks_flushed;
-            chunks_flushed = my_chunks;
-            const int32_t status = status_seen;
-            status_seen = ld_volatile(&A.ctl->status);
+            const unsigned long long add = my_chunks - S.chunks_flushed;
+            S.chunks_flushed = my_chunks;
+            const int32_t status = S.status_seen;
+            S.status_seen = ld_volatile(&A.ctl->status);
             if (status != kStatOk) halt = 1;
-            else if (globaltimer_ns() > deadline) {
+            else if (globaltimer_ns() > S.deadline) {
               atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
               halt = 1;
             } else if (A.max_chunks) {
@@ -1322,8 +1340,8 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           // previous poll, so the poll does not stall the warp
           int want = 0;
           if (lane == 0) {
-            const int32_t asked = requests_seen;
-            requests_seen = ld_volatile(&A.ctl->requests);
+            const int32_t asked = S.requests_seen;
+            S.requests_seen = ld_volatile(&A.ctl->requests);
             // claim one outstanding request: one donation per idle warp's ask
             if (asked > 0) want = atomicSub(&A.ctl->requests, 1) > 0 ? 1 : 2;
           }
@@ -1448,14 +1466,14 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
     }
     if (kBatch) {
       if (lane == 0 && task_count) atomicAdd(&A.counts[pid], task_count);
-    } else {
-      my_count += task_count;
+    } else if (lane == 0) {
+      S.my_count += task_count;
     }
   }
   if (lane == 0) {
     if (!stop) atomicSub(&A.ctl->active, 1);
-    if (my_count) atomicAdd(&A.ctl->count, my_count);
-    if (my_chunks > chunks_flushed) atomicAdd(&A.ctl->chunks, my_chunks - chunks_flushed);
+    if (S.my_count) atomicAdd(&A.ctl->count, S.my_count);
+    if (my_chunks > S.chunks_flushed) atomicAdd(&A.ctl->chunks, my_chunks - S.chunks_flushed);
   }
   if (kC) {
     for (int o = 16; o; o >>= 1) {
