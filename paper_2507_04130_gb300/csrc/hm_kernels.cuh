@@ -656,7 +656,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
       const int32_t fq = mine ? o.c : S.map[cs.q];
       const bool fwd = cs.kind == kOut || cs.kind == kNotOut;
       if (cs.kind <= kIn) {
-        const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
+        const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
         if (r.y == 0) return false;
         if (use_filter(G, r.y) && !arc_maybe_l<kC>(G, fwd ? fq : d, fwd ? d : fq, cs.lab, ctr))
           return false;
@@ -678,7 +678,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
       const int32_t x = fwd ? fq : d, y = fwd ? d : fq;
       int32_t lab;
       if (cs.kind <= kIn) {
-        const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
+        const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
         const bool found =
             use_filter(G, r.y)
                 ? arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab
@@ -714,7 +714,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
     const int32_t q_off_in = mine ? o.off_in : S.off_in[q];
     const bool fwd = cs.kind == kOut || cs.kind == kNotOut;   // arc f(q) -> d ?
     if (cs.kind <= kIn) {
-      const int2 r = mine ? o.own[cs.kind] : grp[P.gbase[p] + j];
+      const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
       const int32_t rev_len = fwd ? vi.z : vi.y;
       if (r.y == 0 || rev_len == 0) return false;
       bool found;
@@ -905,7 +905,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpSta
               hit = true;
             }
         }
-        o.own[cs.kind] = r;
+        if (cs.kind == kOut) o.own[0] = r; else o.own[1] = r;
         lo = (cs.kind == kOut ? of.x : of.y) + r.x;
       } else {
         r = grp[P.gbase[p] + j];
