@@ -387,6 +387,12 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
 // persistent extension kernel
 // ---------------------------------------------------------------------------
 
+// The survivor (image of depth L) a flattened leaf candidate belongs to.
+struct LeafOwner {
+  int32_t c, off_out, off_in, deg_out, deg_in;
+  int2 own[2];  // label group of the leaf inside c's out-list [0] / in-list [1]
+};
+
 struct WarpState {
   int32_t map[kMaxK];       // image of each mapped position
   int32_t deg_out[kMaxK];   // its out-degree
@@ -406,6 +412,10 @@ struct WarpState {
   // count already reported and the last polled status and request words
   unsigned long long deadline, nseeds, seed_at, seed_end, my_count, chunks_flushed;
   int32_t requests_seen, status_seen;
+  // the survivors whose leaf ranges a flattened sweep covers (leaf_flatten),
+  // read by the lanes whose candidates they own
+  LeafOwner owners[32];
+  int4 owner_drive[32];     // {driving condition, range start, its kind, offset in the sweep}
   Task stage;               // task being donated or received
 };
 // Each warp's WarpState is followed in shared memory by one int2 per positive
@@ -627,11 +637,6 @@ __device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, cons
 // descent, where their range can be split and donated.
 constexpr int32_t kFlatMax = 2048;
 
-// The survivor (image of depth L) a flattened leaf candidate belongs to.
-struct LeafOwner {
-  int32_t c, off_out, off_in, deg_out, deg_in;
-  int2 own[2];  // label group of the leaf inside c's out-list [0] / in-list [1]
-};
 
 template <bool kC>
 __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, const WarpState &S,
@@ -847,7 +852,7 @@ __device__ void expand_position1(const DevGraph &G, const Plan &P, const WarpSta
 // at most kFlatMax leaf candidates; returns the survivors left for the
 // ordinary descent.  Adds the matches to task_count and writes their rows.
 template <bool kRows, bool kC, bool kShared>
-__device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpState &S, const ExtArgs &A,
+__device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S, const ExtArgs &A,
                                  int2 *__restrict__ grp, int L, const int32_t *__restrict__ adj,
                                  int32_t base, uint32_t m, int lane, const uint8_t *root_mask,
                                  unsigned long long &task_count, unsigned long long *row_cursor,
@@ -930,6 +935,9 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpSta
   }
   const int32_t excl = incl - len;
   const int32_t total = __shfl_sync(kFull, incl, 31);
+  S.owners[lane] = o;  // lanes without a survivor own an empty range
+  S.owner_drive[lane] = make_int4(drv_j, drv_lo, drv_kind, excl);
+  __syncwarp();
   if (kC && lane == 0 && total) {
     atomicAdd(&ctl->level_chunks[p], (unsigned long long)((total + 31) / 32));
     atomicAdd(&ctl->level_lanes[p], (unsigned long long)total);
@@ -946,20 +954,9 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpSta
       if (g < v) hi_l = mid; else lo_l = mid + 1;
     }
     const int ow = min(lo_l, 31);
-    LeafOwner oo;
-    oo.c = __shfl_sync(kFull, o.c, ow);
-    oo.off_out = __shfl_sync(kFull, o.off_out, ow);
-    oo.off_in = __shfl_sync(kFull, o.off_in, ow);
-    oo.deg_out = __shfl_sync(kFull, o.deg_out, ow);
-    oo.deg_in = __shfl_sync(kFull, o.deg_in, ow);
-    oo.own[0].x = __shfl_sync(kFull, o.own[0].x, ow);
-    oo.own[0].y = __shfl_sync(kFull, o.own[0].y, ow);
-    oo.own[1].x = __shfl_sync(kFull, o.own[1].x, ow);
-    oo.own[1].y = __shfl_sync(kFull, o.own[1].y, ow);
-    const int32_t o_drv_j = __shfl_sync(kFull, drv_j, ow);
-    const int32_t o_drv_lo = __shfl_sync(kFull, drv_lo, ow);
-    const int32_t o_drv_kind = __shfl_sync(kFull, drv_kind, ow);
-    const int32_t o_excl = __shfl_sync(kFull, excl, ow);
+    const LeafOwner &oo = S.owners[ow];
+    const int4 od = S.owner_drive[ow];
+    const int32_t o_drv_j = od.x, o_drv_lo = od.y, o_drv_kind = od.z, o_excl = od.w;
     bool ok = false;
     int32_t d = -1;
     if (g < total) {
@@ -991,6 +988,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, const WarpSta
       }
     }
   }
+  __syncwarp();  // every lane is done with S.owners before the next sweep rewrites it
   return keep;
 }
 
