@@ -943,9 +943,8 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     atomicAdd(&ctl->level_lanes[p], (unsigned long long)total);
   }
   chunks += (unsigned long long)((total + 31) / 32);
-  for (int32_t chunk = 0; chunk < total; chunk += 32) {
-    const int32_t g = chunk + lane;
-    // owner: the first survivor lane whose inclusive prefix exceeds g
+  // owner of sweep position g: the first survivor lane whose inclusive prefix exceeds g
+  auto owner_of = [&](int32_t g) {
     int32_t lo_l = 0, hi_l = 31;
 #pragma unroll
     for (int step = 0; step < 5; ++step) {
@@ -953,17 +952,29 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
       const int32_t v = __shfl_sync(kFull, incl, mid);
       if (g < v) hi_l = mid; else lo_l = mid + 1;
     }
-    const int ow = min(lo_l, 31);
-    const LeafOwner &oo = S.owners[ow];
+    return min(lo_l, 31);
+  };
+  // candidate at sweep position g of owner ow (-1 past the end)
+  auto candidate_at = [&](int32_t g, int ow) {
+    if (g >= total) return -1;
     const int4 od = S.owner_drive[ow];
-    const int32_t o_drv_j = od.x, o_drv_lo = od.y, o_drv_kind = od.z, o_excl = od.w;
-    bool ok = false;
-    int32_t d = -1;
-    if (g < total) {
-      d = __ldg((o_drv_kind == kOut ? G.gout_adj : G.gin_adj) + o_drv_lo + (g - o_excl));
-      if (kC) ctr += 4;
-      ok = check_leaf<kC>(G, P, S, grp, p, o_drv_j, d, oo, root_mask, ctr);
+    if (kC) ctr += 4;
+    return __ldg((od.z == kOut ? G.gout_adj : G.gin_adj) + od.y + (g - od.w));
+  };
+  // the next chunk's owners and candidates are fetched while this chunk is checked
+  int ow_next = owner_of(lane);
+  int32_t d_next = candidate_at(lane, ow_next);
+  for (int32_t chunk = 0; chunk < total; chunk += 32) {
+    const int32_t g = chunk + lane;
+    const int ow = ow_next;
+    const int32_t d = d_next;
+    if (chunk + 32 < total) {
+      ow_next = owner_of(g + 32);
+      d_next = candidate_at(g + 32, ow_next);
     }
+    const LeafOwner &oo = S.owners[ow];
+    bool ok = false;
+    if (g < total) ok = check_leaf<kC>(G, P, S, grp, p, S.owner_drive[ow].x, d, oo, root_mask, ctr);
     if (kShared) {
       expand_position1<kRows, kC>(G, P, S, A, ok, L, oo.c, d, lane, task_count, row_cursor, row_base,
                                   row_cap, ctr);
