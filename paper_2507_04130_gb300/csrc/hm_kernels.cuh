@@ -410,8 +410,13 @@ struct WarpState {
   // registers): the call's deadline, the seed count, this warp's claimed
   // seeds [seed_at, seed_end), its match count and, for lane 0, the chunk
   // count already reported and the last polled status and request words
-  unsigned long long deadline, nseeds, seed_at, seed_end, my_count, chunks_flushed;
+  unsigned long long deadline, nseeds, seed_at, seed_end, my_count;
+  uint32_t chunks_flushed;  // chunk counts run modulo 2^32 and are compared by difference
   int32_t requests_seen, status_seen;
+  // the current task's output: row cursor, first row, rows it may write
+  unsigned long long *row_cursor;
+  int32_t *row_base;
+  unsigned long long row_cap;
   // the survivors whose leaf ranges a flattened sweep covers (leaf_flatten),
   // read by the lanes whose candidates they own
   LeafOwner owners[32];
@@ -855,9 +860,8 @@ template <bool kRows, bool kC, bool kShared>
 __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S, const ExtArgs &A,
                                  int2 *__restrict__ grp, int L, const int32_t *__restrict__ adj,
                                  int32_t base, uint32_t m, int lane, const uint8_t *root_mask,
-                                 unsigned long long &task_count, unsigned long long *row_cursor,
-                                 int32_t *row_base, unsigned long long row_cap, Ctl *ctl,
-                                 unsigned long long &chunks, uint64_t &ctr) {
+                                 unsigned long long &task_count, Ctl *ctl, uint32_t &chunks,
+                                 uint64_t &ctr) {
   const int p = L + 1;
   const int k = P.k;
   const int npos = P.npos[p];
@@ -942,7 +946,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     atomicAdd(&ctl->level_chunks[p], (unsigned long long)((total + 31) / 32));
     atomicAdd(&ctl->level_lanes[p], (unsigned long long)total);
   }
-  chunks += (unsigned long long)((total + 31) / 32);
+  chunks += (uint32_t)((total + 31) / 32);
   // owner of sweep position g: the first survivor lane whose inclusive prefix exceeds g
   auto owner_of = [&](int32_t g) {
     int32_t lo_l = 0, hi_l = 31;
@@ -976,8 +980,8 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     bool ok = false;
     if (g < total) ok = check_leaf<kC>(G, P, S, grp, p, S.owner_drive[ow].x, d, oo, root_mask, ctr);
     if (kShared) {
-      expand_position1<kRows, kC>(G, P, S, A, ok, L, oo.c, d, lane, task_count, row_cursor, row_base,
-                                  row_cap, ctr);
+      expand_position1<kRows, kC>(G, P, S, A, ok, L, oo.c, d, lane, task_count, S.row_cursor, S.row_base,
+                                  S.row_cap, ctr);
       continue;
     }
     const uint32_t bal = __ballot_sync(kFull, ok);
@@ -985,13 +989,13 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     task_count += nm;
     if (kRows && nm) {
       unsigned long long at = 0;
-      if (lane == 0) at = atomicAdd(row_cursor, (unsigned long long)nm);
+      if (lane == 0) at = atomicAdd(S.row_cursor, (unsigned long long)nm);
       at = __shfl_sync(kFull, at, 0);
       if (ok) {
         const unsigned long long r = at + __popc(bal & lanemask_lt());
-        if (r < row_cap) {
+        if (r < S.row_cap) {
           if (kC) ctr += 4 * k;
-          int32_t *row = row_base + r * k;
+          int32_t *row = S.row_base + r * k;
           for (int i = 0; i < L; ++i) row[P.orig[i]] = S.map[i];
           row[P.orig[L]] = oo.c;
           row[P.orig[p]] = d;
@@ -1161,7 +1165,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
     S.status_seen = kStatOk;
   }
   __syncwarp();
-  unsigned long long my_chunks = 0, next_check = 64, next_poll = A.poll_mask + 1ull;
+  uint32_t my_chunks = 0, next_check = 64, next_poll = A.poll_mask + 1u;
   bool seeds_done = false, stop = false;
   if (lane == 0) atomicAdd(&A.ctl->active, 1);
 
@@ -1256,9 +1260,12 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
     if (got == 2 && kBatch) pid = S.stage.pid;
     const Plan &P = kBatch ? A.plans[pid] : P0;
     const int k = P.k;
-    unsigned long long *const row_cursor = kBatch ? A.row_cursor + pid : &A.ctl->rows_written;
-    int32_t *const row_base = kBatch ? A.rows + A.row_off[pid] : A.rows;
-    const unsigned long long row_cap = kBatch ? A.row_cap[pid] : A.cap;
+    if (kRows && lane == 0) {
+      S.row_cursor = kBatch ? A.row_cursor + pid : &A.ctl->rows_written;
+      S.row_base = kBatch ? A.rows + A.row_off[pid] : A.rows;
+      S.row_cap = kBatch ? A.row_cap[pid] : A.cap;
+    }
+    __syncwarp();
     unsigned long long task_count = 0;
     if (got == 1) {
       if (kBatch && k == 2) {
@@ -1266,10 +1273,10 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         if (lane == 0) {
           atomicAdd(&A.counts[pid], 1ull);
           if (kRows) {
-            const unsigned long long r = atomicAdd(row_cursor, 1ull);
-            if (r < row_cap) {
-              row_base[r * 2 + P.orig[0]] = S.map[0];
-              row_base[r * 2 + P.orig[1]] = S.map[1];
+            const unsigned long long r = atomicAdd(S.row_cursor, 1ull);
+            if (r < S.row_cap) {
+              S.row_base[r * 2 + P.orig[0]] = S.map[0];
+              S.row_base[r * 2 + P.orig[1]] = S.map[1];
             }
           }
         }
@@ -1316,13 +1323,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           continue;
         }
         ++my_chunks;
-        if (my_chunks >= next_check) {
+        if ((int32_t)(my_chunks - next_check) >= 0) {
           // budget check every 64 chunks; the status word read here was
           // requested at the previous check, so its latency is hidden
           next_check = my_chunks + 64;
           int halt = 0;
           if (lane == 0) {
-            const unsigned long long add = my_chunks - S.chunks_flushed;
+            const unsigned long long add = my_chunks - S.chunks_flushed;  // modulo 2^32
             S.chunks_flushed = my_chunks;
             const int32_t status = S.status_seen;
             S.status_seen = ld_volatile(&A.ctl->status);
@@ -1342,8 +1349,8 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           }
           if (__shfl_sync(kFull, halt, 0)) { stop = true; break; }
         }
-        if (my_chunks >= next_poll) {
-          next_poll = my_chunks + A.poll_mask + 1ull;
+        if ((int32_t)(my_chunks - next_poll) >= 0) {
+          next_poll = my_chunks + A.poll_mask + 1u;
           // donate only while fewer tasks wait in the queue than warps wait
           // for work; the idle-warp count used is the one requested at the
           // previous poll, so the poll does not stall the warp
@@ -1420,8 +1427,8 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         }
         if (kShared && leaf) {
           // leaf of a shared position-0 state: choose position 1 for each survivor
-          expand_position1<kRows, kC>(G, P, S, A, ok, k - 1, -1, c, lane, task_count, row_cursor, row_base,
-                                      row_cap, ctr);
+          expand_position1<kRows, kC>(G, P, S, A, ok, k - 1, -1, c, lane, task_count, S.row_cursor,
+                                      S.row_base, S.row_cap, ctr);
           __syncwarp();
           continue;
         }
@@ -1431,13 +1438,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           task_count += nm;
           if (kRows && nm) {
             unsigned long long at = 0;
-            if (lane == 0) at = atomicAdd(row_cursor, (unsigned long long)nm);
+            if (lane == 0) at = atomicAdd(S.row_cursor, (unsigned long long)nm);
             at = __shfl_sync(kFull, at, 0);
             if (ok) {
               unsigned long long r = at + __popc(m & lanemask_lt());
-              if (r < row_cap) {
+              if (r < S.row_cap) {
                 if (kC) ctr += 4 * k;
-                int32_t *row = row_base + r * k;
+                int32_t *row = S.row_base + r * k;
                 for (int i = 0; i < k - 1; ++i) row[P.orig[i]] = S.map[i];
                 row[P.orig[k - 1]] = c;
               }
@@ -1449,8 +1456,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         uint32_t pending = m;
         if (A.leaf_flatten && level == k - 2 && m)
           pending = leaf_flatten<kRows, kC, kShared>(G, P, S, A, grp, level, adj, lo, m, lane, A.root_mask,
-                                            task_count, row_cursor, row_base, row_cap, A.ctl,
-                                            my_chunks, ctr);
+                                            task_count, A.ctl, my_chunks, ctr);
         if (lane == 0) {
           S.mask[level] = pending;
           S.base[level] = lo;
@@ -1482,7 +1488,8 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
   if (lane == 0) {
     if (!stop) atomicSub(&A.ctl->active, 1);
     if (S.my_count) atomicAdd(&A.ctl->count, S.my_count);
-    if (my_chunks > S.chunks_flushed) atomicAdd(&A.ctl->chunks, my_chunks - S.chunks_flushed);
+    if (my_chunks != S.chunks_flushed)
+      atomicAdd(&A.ctl->chunks, (unsigned long long)(uint32_t)(my_chunks - S.chunks_flushed));
   }
   if (kC) {
     for (int o = 16; o; o >>= 1) {
