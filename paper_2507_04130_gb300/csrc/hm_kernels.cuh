@@ -585,7 +585,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
 // The lane with `base` set also applies the per-candidate checks
 // (injectivity, root mask, degree filter on inner levels).
 template <bool kC>
-__device__ __forceinline__ bool check_one(const DevGraph &G, const Plan &P, const WarpState &S,
+__device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const WarpState &S,
                                           const int2 *__restrict__ grp, int p, int j, int32_t c,
                                           bool base, bool leaf, const uint8_t *root_mask,
                                           uint64_t &ctr) {
@@ -1009,7 +1009,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
 
 // ---- bounded lock-free queue (Vyukov-style sequence numbers) --------------
 
-__device__ bool q_push(const ExtArgs &A, WarpState &S, int lane) {
+__device__ __noinline__ bool q_push(const ExtArgs &A, WarpState &S, int lane) {
   long long pos = -1;
   if (lane == 0) {
     atomic_u64 tail(A.ctl->tail);
@@ -1043,7 +1043,7 @@ __device__ bool q_push(const ExtArgs &A, WarpState &S, int lane) {
   return true;
 }
 
-__device__ bool q_pop(const ExtArgs &A, WarpState &S, int lane) {
+__device__ __noinline__ bool q_pop(const ExtArgs &A, WarpState &S, int lane) {
   long long pos = -1;
   if (lane == 0) {
     atomic_u64 head(A.ctl->head);
@@ -1089,7 +1089,7 @@ __device__ __forceinline__ bool queue_maybe_nonempty(const ExtArgs &A) {
 // The task being run may restrict its first chunk [first_lo, first_lo + 32) at
 // depth L0 to the candidates in first_mask; a split of that window hands the
 // shifted restriction to the new task (such tasks never extend past the window).
-__device__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0, int level,
+__device__ __noinline__ bool try_donate(const ExtArgs &A, const Plan &P, WarpState &S, int L0, int level,
                            int lane, int32_t first_lo, uint32_t first_mask, int32_t pid) {
   int l = -1, kind = 0;
   for (int d = L0; d <= level; ++d) {
