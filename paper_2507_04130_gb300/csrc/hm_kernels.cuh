@@ -1141,6 +1141,92 @@ __device__ __noinline__ bool try_donate(const ExtArgs &A, const Plan &P, WarpSta
   return pushed;
 }
 
+// An idle warp advertises itself and waits, with backoff, for a donated task
+// or for global quiescence, every wait bounded by the call's deadline.
+// Returns true with a task installed in S.stage, false when the call is over.
+__device__ __noinline__ bool idle_wait(const ExtArgs &A, WarpState &S, int lane) {
+  if (lane == 0) {
+    atomicAdd(&A.ctl->hungry, 1);
+    atomicAdd(&A.ctl->requests, 1);
+    atomicSub(&A.ctl->active, 1);
+  }
+  unsigned ns = 64;
+  for (;;) {
+    int quit = 0;
+    if (lane == 0) {
+      if (ld_volatile(&A.ctl->status) != kStatOk) quit = 1;
+      else if (globaltimer_ns() > S.deadline) {
+        atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
+        quit = 1;
+      } else {
+        __threadfence();
+        int32_t act = ld_volatile(&A.ctl->active);
+        __threadfence();
+        if (act == 0 && !queue_maybe_nonempty(A)) quit = 1;
+      }
+      if (!quit && queue_maybe_nonempty(A)) {
+        atomicAdd(&A.ctl->active, 1);
+        quit = 2;  // try to take it
+      }
+    }
+    quit = __shfl_sync(kFull, quit, 0);
+    if (quit == 1) {
+      if (lane == 0) atomicSub(&A.ctl->hungry, 1);
+      return false;
+    }
+    if (quit == 2) {
+      if (q_pop(A, S, lane)) {
+        if (lane == 0) atomicSub(&A.ctl->hungry, 1);
+        return true;
+      }
+      if (lane == 0) atomicSub(&A.ctl->active, 1);
+    }
+    __nanosleep(ns);
+    ns = min(ns * 2, 4096u);
+  }
+}
+
+// Every 64 chunks: report them, and stop when the call's status is no longer
+// ok, its deadline has passed or its chunk budget is spent.  Warp-uniform.
+__device__ __noinline__ bool budget_check(const ExtArgs &A, WarpState &S, int lane, uint32_t my_chunks) {
+  int halt = 0;
+  if (lane == 0) {
+    // the status word read here was requested at the previous check, so its
+    // latency is hidden
+    const unsigned long long add = (uint32_t)(my_chunks - S.chunks_flushed);  // modulo 2^32
+    S.chunks_flushed = my_chunks;
+    const int32_t status = S.status_seen;
+    S.status_seen = ld_volatile(&A.ctl->status);
+    if (status != kStatOk) halt = 1;
+    else if (globaltimer_ns() > S.deadline) {
+      atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
+      halt = 1;
+    } else if (A.max_chunks) {
+      unsigned long long tot = atomicAdd(&A.ctl->chunks, add) + add;
+      if (tot > A.max_chunks) {
+        atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
+        halt = 1;
+      }
+    } else {
+      atomicAdd(&A.ctl->chunks, add);
+    }
+  }
+  return __shfl_sync(kFull, halt, 0) != 0;
+}
+
+// Every poll_mask+1 chunks: claim one outstanding donation request.  The
+// request count used is the one read at the previous poll, so the poll does
+// not stall the warp.  0: nothing to do; 1: donate; 2: no request claimed.
+__device__ __noinline__ int poll_requests(const ExtArgs &A, WarpState &S, int lane) {
+  int want = 0;
+  if (lane == 0) {
+    const int32_t asked = S.requests_seen;
+    S.requests_seen = ld_volatile(&A.ctl->requests);
+    if (asked > 0) want = atomicSub(&A.ctl->requests, 1) > 0 ? 1 : 2;
+  }
+  return __shfl_sync(kFull, want, 0);
+}
+
 __host__ __device__ constexpr size_t warp_smem_bytes(int ngrp) {
   return (sizeof(WarpState) + sizeof(int2) * (size_t)ngrp + 15) / 16 * 16;
 }
@@ -1214,48 +1300,11 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
     }
     if (!got && q_pop(A, S, lane)) got = 2;
     if (!got) {
-      // go idle: advertise, and wait for a donation or for global quiescence
-      if (lane == 0) {
-        atomicAdd(&A.ctl->hungry, 1);
-        atomicAdd(&A.ctl->requests, 1);
-        atomicSub(&A.ctl->active, 1);
-      }
-      unsigned ns = 64;
-      for (;;) {
-        int quit = 0;
-        if (lane == 0) {
-          if (ld_volatile(&A.ctl->status) != kStatOk) quit = 1;
-          else if (globaltimer_ns() > S.deadline) {
-            atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
-            quit = 1;
-          } else {
-            __threadfence();
-            int32_t act = ld_volatile(&A.ctl->active);
-            __threadfence();
-            if (act == 0 && !queue_maybe_nonempty(A)) quit = 1;
-          }
-          if (!quit && queue_maybe_nonempty(A)) {
-            atomicAdd(&A.ctl->active, 1);
-            quit = 2;  // try to take it
-          }
-        }
-        quit = __shfl_sync(kFull, quit, 0);
-        if (quit == 1) { stop = true; break; }
-        if (quit == 2) {
-          if (q_pop(A, S, lane)) {
-            got = 2;
-            if (lane == 0) atomicSub(&A.ctl->hungry, 1);
-            break;
-          }
-          if (lane == 0) atomicSub(&A.ctl->active, 1);
-        }
-        __nanosleep(ns);
-        ns = min(ns * 2, 4096u);
-      }
-      if (stop) {
-        if (lane == 0) atomicSub(&A.ctl->hungry, 1);
+      if (!idle_wait(A, S, lane)) {
+        stop = true;
         break;
       }
+      got = 2;
     }
     if (got == 2 && kBatch) pid = S.stage.pid;
     const Plan &P = kBatch ? A.plans[pid] : P0;
@@ -1324,44 +1373,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         }
         ++my_chunks;
         if ((int32_t)(my_chunks - next_check) >= 0) {
-          // budget check every 64 chunks; the status word read here was
-          // requested at the previous check, so its latency is hidden
           next_check = my_chunks + 64;
-          int halt = 0;
-          if (lane == 0) {
-            const unsigned long long add = my_chunks - S.chunks_flushed;  // modulo 2^32
-            S.chunks_flushed = my_chunks;
-            const int32_t status = S.status_seen;
-            S.status_seen = ld_volatile(&A.ctl->status);
-            if (status != kStatOk) halt = 1;
-            else if (globaltimer_ns() > S.deadline) {
-              atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
-              halt = 1;
-            } else if (A.max_chunks) {
-              unsigned long long tot = atomicAdd(&A.ctl->chunks, add) + add;
-              if (tot > A.max_chunks) {
-                atomicCAS(&A.ctl->status, kStatOk, kStatBudget);
-                halt = 1;
-              }
-            } else {
-              atomicAdd(&A.ctl->chunks, add);
-            }
-          }
-          if (__shfl_sync(kFull, halt, 0)) { stop = true; break; }
+          if (budget_check(A, S, lane, my_chunks)) { stop = true; break; }
         }
         if ((int32_t)(my_chunks - next_poll) >= 0) {
           next_poll = my_chunks + A.poll_mask + 1u;
-          // donate only while fewer tasks wait in the queue than warps wait
-          // for work; the idle-warp count used is the one requested at the
-          // previous poll, so the poll does not stall the warp
-          int want = 0;
-          if (lane == 0) {
-            const int32_t asked = S.requests_seen;
-            S.requests_seen = ld_volatile(&A.ctl->requests);
-            // claim one outstanding request: one donation per idle warp's ask
-            if (asked > 0) want = atomicSub(&A.ctl->requests, 1) > 0 ? 1 : 2;
-          }
-          want = __shfl_sync(kFull, want, 0);
+          // one donation per idle warp's request
+          const int want = poll_requests(A, S, lane);
           if (want) {
             bool gave = false;
             if (want == 1) {
