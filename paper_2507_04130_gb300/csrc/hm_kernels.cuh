@@ -643,6 +643,55 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
 constexpr int32_t kFlatMax = 2048;
 
 
+// check_leaf's conditions without the arc filter (arc_filter = -1): each one
+// searches the shorter of f(q)'s list and d's reverse list.  Out of line: the
+// default path never runs it.
+template <bool kC>
+__device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &P, const WarpState &S,
+                                                 const int2 *__restrict__ grp, int p, int drive, int32_t d,
+                                                 const LeafOwner &o, uint64_t &ctr) {
+  const int L = p - 1;
+  const int nc = P.ncons[p];
+  if (kC) ctr += 32;
+  const int4 vi = __ldg(&G.vi[d]);
+  const int2 od = __ldg(&G.off[d]);
+  for (int j = 0; j < nc; ++j) {
+    if (j == drive) continue;
+    const Cons cs = P.cons[p][j];
+    const int q = cs.q;
+    const bool mine = q == L;
+    const int32_t fq = mine ? o.c : S.map[q];
+    const int32_t q_off_out = mine ? o.off_out : S.off_out[q];
+    const int32_t q_off_in = mine ? o.off_in : S.off_in[q];
+    const bool fwd = cs.kind == kOut || cs.kind == kNotOut;   // arc f(q) -> d ?
+    if (cs.kind <= kIn) {
+      const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
+      const int32_t rev_len = fwd ? vi.z : vi.y;
+      if (r.y == 0 || rev_len == 0) return false;
+      bool found;
+      if (rev_len < r.y) {
+        const int32_t i = fwd ? search_c<kC>(G.in_adj, od.y, rev_len, fq, ctr)
+                              : search_c<kC>(G.out_adj, od.x, rev_len, fq, ctr);
+        if (kC && i >= 0) ctr += 4;
+        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+      } else {
+        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, (fwd ? q_off_out : q_off_in) + r.x, r.y,
+                             d, ctr) >= 0;
+      }
+      if (!found) return false;
+    } else {
+      const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[q]) : (mine ? o.deg_in : S.deg_in[q]);
+      const int32_t lb = fwd ? vi.z : vi.y;
+      if (la == 0 || lb == 0) continue;
+      const bool found =
+          la <= lb ? search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? q_off_out : q_off_in, la, d, ctr) >= 0
+                   : search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? od.y : od.x, lb, fq, ctr) >= 0;
+      if (found) return false;
+    }
+  }
+  return true;
+}
+
 template <bool kC>
 __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, const WarpState &S,
                                            const int2 *__restrict__ grp, int p, int drive, int32_t d,
@@ -709,46 +758,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
     }
     return true;
   }
-  // without the filter: search the shorter of f(q)'s list and d's reverse list
-  const uint64_t settled = 0;
-  if (kC) ctr += 32;
-  const int4 vi = __ldg(&G.vi[d]);
-  const int2 od = __ldg(&G.off[d]);
-  for (int j = 0; j < nc; ++j) {
-    if (j == drive || ((settled >> j) & 1)) continue;
-    const Cons cs = P.cons[p][j];
-    const int q = cs.q;
-    const bool mine = q == L;
-    const int32_t fq = mine ? o.c : S.map[q];
-    const int32_t q_off_out = mine ? o.off_out : S.off_out[q];
-    const int32_t q_off_in = mine ? o.off_in : S.off_in[q];
-    const bool fwd = cs.kind == kOut || cs.kind == kNotOut;   // arc f(q) -> d ?
-    if (cs.kind <= kIn) {
-      const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
-      const int32_t rev_len = fwd ? vi.z : vi.y;
-      if (r.y == 0 || rev_len == 0) return false;
-      bool found;
-      if (rev_len < r.y) {
-        const int32_t i = fwd ? search_c<kC>(G.in_adj, od.y, rev_len, fq, ctr)
-                              : search_c<kC>(G.out_adj, od.x, rev_len, fq, ctr);
-        if (kC && i >= 0) ctr += 4;
-        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
-      } else {
-        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, (fwd ? q_off_out : q_off_in) + r.x, r.y,
-                             d, ctr) >= 0;
-      }
-      if (!found) return false;
-    } else {
-      const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[q]) : (mine ? o.deg_in : S.deg_in[q]);
-      const int32_t lb = fwd ? vi.z : vi.y;
-      if (la == 0 || lb == 0) continue;
-      const bool found =
-          la <= lb ? search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? q_off_out : q_off_in, la, d, ctr) >= 0
-                   : search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? od.y : od.x, lb, fq, ctr) >= 0;
-      if (found) return false;
-    }
-  }
-  return true;
+  return check_leaf_searched<kC>(G, P, S, grp, p, drive, d, o, ctr);
 }
 
 // ---- shared position-0 states: choosing position 1 last ---------------------
