@@ -431,28 +431,19 @@ template <bool kC>
 __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int pos, int32_t c,
                                            int lane, uint64_t &ctr) {
   if (kC && lane == 0) ctr += 48;
-  // three independent 16-byte loads spread over three lanes
-  int4 vi = make_int4(0, 0, 0, 0), vd = make_int4(0, 0, 0, 0);
-  int2 o = make_int2(0, 0);
-  if (c >= 0) {  // c < 0: position 1 of a shared position-0 state, not yet chosen
-    if (lane == 0) vi = __ldg(&G.vi[c]);
-    if (lane == 1) o = __ldg(&G.off[c]);
-    if (lane == 2) vd = __ldg(&G.vdir[c]);
-  }
-  const int32_t dout = __shfl_sync(kFull, vi.y, 0), din = __shfl_sync(kFull, vi.z, 0);
-  const int32_t oo = __shfl_sync(kFull, o.x, 1), oi = __shfl_sync(kFull, o.y, 1);
-  int4 d;
-  d.x = __shfl_sync(kFull, vd.x, 2);
-  d.y = __shfl_sync(kFull, vd.y, 2);
-  d.z = __shfl_sync(kFull, vd.z, 2);
-  d.w = __shfl_sync(kFull, vd.w, 2);
+  // three independent 16-byte loads, each lane writing its own record's fields
+  const bool known = c >= 0;  // c < 0: position 1 of a shared position-0 state, not yet chosen
   if (lane == 0) {
+    const int4 vi = known ? __ldg(&G.vi[c]) : make_int4(0, 0, 0, 0);
     S.map[pos] = c;
-    S.deg_out[pos] = dout;
-    S.deg_in[pos] = din;
-    S.off_out[pos] = oo;
-    S.off_in[pos] = oi;
-    S.dir[pos] = d;
+    S.deg_out[pos] = vi.y;
+    S.deg_in[pos] = vi.z;
+  } else if (lane == 1) {
+    const int2 o = known ? __ldg(&G.off[c]) : make_int2(0, 0);
+    S.off_out[pos] = o.x;
+    S.off_in[pos] = o.y;
+  } else if (lane == 2) {
+    S.dir[pos] = known ? __ldg(&G.vdir[c]) : make_int4(0, 0, 0, 0);
   }
 }
 
