@@ -14,8 +14,9 @@
 //                      (64 MB for 16M arcs, within the 129 MB L2)
 //   ahash    int4[2*H] arc hash table: H = m buckets of two 16-byte slots
 //                      {u, v, label, 0} (32 bytes per arc, half the slots used)
-// A vertex's label and both degrees arrive in one 16-byte load; its list
-// offsets in a second one, fetched only when a list is actually searched.
+// A vertex's label and both degrees arrive in one 16-byte load, its list
+// offsets in a second one.  The label-grouped lists and their directory
+// (gout_adj, gin_adj, gdir_out, gdir_in, vdir) are described with DevGraph.
 #pragma once
 
 #include <cuda_runtime.h>

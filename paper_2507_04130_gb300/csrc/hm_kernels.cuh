@@ -6,26 +6,31 @@
 //                   pattern arc between positions 0 and 1 (the loop "for all
 //                   e in E2" of the HiPerMotif algorithm): vertex validator
 //                   (Alg. 2) on the position-0 image, edge validator (Alg. 3)
-//                   label, opposite-arc and degree checks.  Arcs stream in
-//                   CSR order with int4 loads; survivors are compacted with
-//                   warp ballots and a block scan into the seed queue.
+//                   label, opposite-arc and degree checks.  Each block streams
+//                   one contiguous span of the arcs in CSR order with int4
+//                   loads (the next step's already in flight); survivors go
+//                   through per-warp shared buffers into the seed queue.
 //   k_seed_overlap  the edge validator's neighbour-overlap test
 //                   |N_u & N_v| >= |N_0 & N_1|, one warp per surviving arc,
 //                   launched only when the right side is non-zero.
 //   k_extend        state injection and extension: each seed is a depth-2
 //                   partial mapping; a persistent kernel extends it vertex by
 //                   vertex, one warp per state.  At each depth the candidates
-//                   are the shortest anchor list (the out- or in-list of an
-//                   already-mapped neighbour), scanned 32 at a time; each lane
-//                   checks one candidate (injectivity, label, degrees, the
-//                   other arcs by binary search, induced non-arcs) and a
-//                   ballot gives the survivors.  The depth-first stack lives in
-//                   shared memory.  At the last inner depth the survivors'
-//                   leaf ranges are swept together (leaf_flatten).  Idle warps
-//                   post donation requests; a busy warp claims one and splits
-//                   off half of its shallowest unfinished range through a
-//                   bounded lock-free queue.  Every wait is bounded by the
-//                   call's time budget.
+//                   are the shortest label-compatible anchor range (part of
+//                   the out- or in-list of an already-mapped neighbour),
+//                   scanned 32 at a time; each lane checks one candidate
+//                   (injectivity, degrees, the other pattern arcs and the
+//                   induced non-arcs through the arc filter and hash table,
+//                   or a binary search for short lists) and a ballot gives
+//                   the survivors.  The depth-first stack lives in shared
+//                   memory.  At the last inner depth the survivors' leaf
+//                   ranges are swept together (leaf_flatten).  Idle warps post
+//                   donation requests; a busy warp claims one and splits off
+//                   half of its shallowest unfinished range through a bounded
+//                   lock-free queue.  Every wait is bounded by the call's time
+//                   budget.  For monomorphism with a pendant position 1 the
+//                   seeds of one position-0 image share one search
+//                   (expand_position1).
 //   k_seed_rows     two-vertex patterns: each seed is already a match.
 //
 // Output: a match count (uint64), and optionally rows in original pattern
