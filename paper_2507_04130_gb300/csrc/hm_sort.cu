@@ -20,6 +20,7 @@
 //              (stability), and rows are copied to their final slots.
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
 
 #include "hm_internal.cuh"
 
@@ -176,10 +177,145 @@ k_scatter(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nro
   }
 }
 
+// The same pass for four-word rows (the arc rows of the graph build and the
+// matches of 4-vertex patterns), with coalesced writes: each row is loaded
+// once as an int4, the tile is reordered by digit in shared memory, and the
+// tile's run of each digit is written out by consecutive threads.
+__device__ __forceinline__ uint32_t digit_of4(int4 r, const KeySpec &ks) {
+  const int32_t w[4] = {r.x, r.y, r.z, r.w};
+  uint32_t v = 0;
+  int got = 0;
+  int col_lo = 0;
+#pragma unroll
+  for (int i = kMaxKeyCols - 1; i >= 0; --i) {
+    if (i >= ks.ncols || got >= kDigitBits) continue;
+    const int b = ks.bits[i];
+    const int want_lo = ks.shift + got;
+    if (want_lo < col_lo + b) {
+      const int r0 = want_lo - col_lo;
+      const int take = min(b - r0, kDigitBits - got);
+      const int c = ks.cols[i];
+      const uint32_t col = (uint32_t)(c == 0 ? w[0] : c == 1 ? w[1] : c == 2 ? w[2] : w[3]) ^ ks.xr[i];
+      v |= ((col >> r0) & ((take >= 32) ? 0xffffffffu : ((1u << take) - 1u))) << got;
+      got += take;
+    }
+    col_lo += b;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, int64_t per_block, KeySpec ks,
+           const uint32_t *__restrict__ starts, int grid) {
+  __shared__ uint32_t s_base[kRadix];                  // global start of each digit for this block
+  __shared__ uint16_t s_cnt[kSortWarps][kRadix];       // per-warp digit counts, then warp offsets
+  __shared__ uint16_t s_first[kRadix];                 // tile-local start of each digit
+  __shared__ uint16_t s_num[kRadix];                   // tile count of each digit
+  __shared__ int4 s_rows[kTile];                       // the tile in digit order
+  __shared__ uint16_t s_dig[kTile];                    // digit of each reordered row
+  __shared__ uint32_t s_wsum[kSortWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    s_base[d] = starts[(int64_t)d * grid + blockIdx.x];
+  const int64_t lo = (int64_t)blockIdx.x * per_block;
+  const int64_t hi = min(nrows, lo + per_block);
+  const uint32_t lt = lanemask_lt();
+  for (int64_t tile = lo; tile < hi; tile += kTile) {
+    const int tn = (int)min((int64_t)kTile, hi - tile);
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
+    __syncthreads();
+    int4 row[kItems];
+    uint32_t dig[kItems], rank[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int li = warp * 32 * kItems + r * 32 + lane;
+      const bool valid = li < tn;
+      row[r] = valid ? in[tile + li] : make_int4(0, 0, 0, 0);
+      const uint32_t d = valid ? digit_of4(row[r], ks) : kRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t prev = 0;
+      if (valid && lane == leader) {
+        prev = s_cnt[warp][d];
+        s_cnt[warp][d] = (uint16_t)(prev + __popc(peers));
+      }
+      prev = __shfl_sync(0xffffffffu, prev, leader);
+      dig[r] = d;
+      rank[r] = prev + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: warp offsets (in place) and the tile count
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t t = s_cnt[w][d];
+        s_cnt[w][d] = (uint16_t)acc;
+        acc += t;
+      }
+      s_num[d] = (uint16_t)acc;
+    }
+    __syncthreads();
+    // tile-local start of each digit: exclusive scan of s_num (kRadix / kSortThreads per thread)
+    {
+      constexpr int kPer = kRadix / kSortThreads;
+      uint32_t v[kPer], sum = 0;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        v[t] = s_num[threadIdx.x * kPer + t];
+        sum += v[t];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      uint32_t before = x - sum;
+      for (int w = 0; w < warp; ++w) before += s_wsum[w];
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        s_first[threadIdx.x * kPer + t] = (uint16_t)before;
+        before += v[t];
+      }
+    }
+    __syncthreads();
+    // reorder the tile by digit in shared memory
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int li = warp * 32 * kItems + r * 32 + lane;
+      if (li < tn) {
+        const uint32_t d = dig[r];
+        const int lp = s_first[d] + s_cnt[warp][d] + rank[r];
+        s_rows[lp] = row[r];
+        s_dig[lp] = (uint16_t)d;
+      }
+    }
+    __syncthreads();
+    // consecutive threads write consecutive rows of each digit's run
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+      const uint32_t d = s_dig[t];
+      out[(int64_t)s_base[d] + (t - s_first[d])] = s_rows[t];
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) s_base[d] += s_num[d];
+    __syncthreads();
+  }
+}
+
 template <int W>
 void launch_scatter(const int32_t *in, int32_t *out, int64_t nrows, int64_t per_block, KeySpec ks,
                     const uint32_t *starts, int grid, cudaStream_t s) {
-  k_scatter<W><<<grid, kSortThreads, 0, s>>>(in, out, nrows, per_block, ks, starts, grid);
+  // int4 rows need 16-byte aligned buffers (a caller's output buffer may not be)
+  const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+  if (W == 4 && aligned)
+    k_scatter4<<<grid, kSortThreads, 0, s>>>(reinterpret_cast<const int4 *>(in), reinterpret_cast<int4 *>(out),
+                                             nrows, per_block, ks, starts, grid);
+  else
+    k_scatter<W><<<grid, kSortThreads, 0, s>>>(in, out, nrows, per_block, ks, starts, grid);
 }
 
 using ScatterFn = void (*)(const int32_t *, int32_t *, int64_t, int64_t, KeySpec,

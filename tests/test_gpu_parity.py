@@ -516,3 +516,19 @@ def test_shared_position0_states_rooted_and_parts(hm):
                 s += c
             assert s == total
         assert sum(hm.count_matches_part(G, P, mode, i, 3) for i in range(3)) == total
+
+
+def test_rows_into_an_unaligned_output_buffer(hm):
+    """A caller's row buffer need not be 16-byte aligned (the sort then takes its generic path)."""
+    g = synth.config2_graph(scale=11)
+    G = hm.Graph.from_synth(g)
+    og = oracle.OracleGraph.from_synth(g)
+    sp = synth.config2_patterns()[1]
+    P = hm.Pattern.from_synth(sp)
+    want_c, want_r = og.match(sp, oracle.INDUCED)
+    assert want_c > 1
+    big = torch.empty(want_c * sp.k + 1, dtype=torch.int32, device="cuda")
+    out = big[1:]                       # 4-byte offset
+    assert out.data_ptr() % 16 != 0
+    rows = hm.enumerate_matches(G, P, hm.INDUCED, out=out, capacity=want_c)
+    np.testing.assert_array_equal(rows.cpu().numpy(), want_r)
