@@ -125,6 +125,48 @@ k_edge_seed_batch(const __grid_constant__ DevGraph G, const Plan *__restrict__ p
   }
 }
 
+// Before the overlap test: seeds of patterns without one go straight to the
+// output (out / nout); the others are gathered for the test (test / ntest).
+// One thread per seed, warp-aggregated appends, so the warp-per-seed test
+// runs only where a pattern asks for it.
+__global__ void __launch_bounds__(kSeedThreads)
+k_overlap_split(const Plan *__restrict__ plans, const int2 *__restrict__ in, const int32_t *__restrict__ pid_in,
+                const unsigned long long *__restrict__ nin, int2 *__restrict__ out, int32_t *__restrict__ pid_out,
+                unsigned long long *__restrict__ nout, int2 *__restrict__ test, int32_t *__restrict__ pid_test,
+                unsigned long long *__restrict__ ntest) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const unsigned long long n = *nin;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += stride) {
+    const unsigned long long i = base + lane;
+    const bool valid = i < n;
+    const int32_t pid = valid ? pid_in[i] : 0;
+    const int2 uv = valid ? in[i] : make_int2(0, 0);
+    const bool pass = valid && plans[pid].ov_need == 0;
+    const bool tst = valid && !pass;
+    const uint32_t bp = __ballot_sync(kFull, pass), bt = __ballot_sync(kFull, tst);
+    unsigned long long op = 0, ot = 0;
+    if (lane == 0) {
+      if (bp) op = atomicAdd(nout, (unsigned long long)__popc(bp));
+      if (bt) ot = atomicAdd(ntest, (unsigned long long)__popc(bt));
+    }
+    op = __shfl_sync(kFull, op, 0);
+    ot = __shfl_sync(kFull, ot, 0);
+    if (pass) {
+      const unsigned long long at = op + __popc(bp & lt);
+      out[at] = uv;
+      pid_out[at] = pid;
+    }
+    if (tst) {
+      const unsigned long long at = ot + __popc(bt & lt);
+      test[at] = uv;
+      pid_test[at] = pid;
+    }
+  }
+}
+
 // Rows of every pattern, padded to width kmax+1 with the pattern id first.
 __global__ void k_pack_rows(const int32_t *__restrict__ rows, const unsigned long long *__restrict__ off,
                             const unsigned long long *__restrict__ start, const int32_t *__restrict__ ks,
@@ -288,10 +330,21 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   const unsigned long long *nseeds = &ctl->nseeds_raw;
   Timer t_ov(s, timing && any_ov);
   if (any_ov && nraw) {
-    k_seed_overlap<false, true><<<sms * 8, kSeedThreads, 0, s>>>(G, 0, seeds_a, &ctl->nseeds_raw, seeds_b,
-                                                                  nraw, &ctl->nseeds, &ctl->bytes_overlap,
-                                                                  d_plans, pid_a, pid_b);
-    launches += 1;
+    int2 *seeds_c;
+    int32_t *pid_c;
+    unsigned long long *ntest;
+    HM_CUDA_TRY(sc.get((void **)&seeds_c, sizeof(int2) * (size_t)nraw));
+    HM_CUDA_TRY(sc.get((void **)&pid_c, sizeof(int32_t) * (size_t)nraw));
+    HM_CUDA_TRY(sc.get((void **)&ntest, sizeof(unsigned long long)));
+    HM_CUDA_TRY(cudaMemsetAsync(ntest, 0, sizeof(unsigned long long), s));
+    const int grid_s = (int)std::max<unsigned long long>(
+        1, std::min<unsigned long long>((nraw + kSeedThreads - 1) / kSeedThreads, (unsigned long long)sms * 8));
+    k_overlap_split<<<grid_s, kSeedThreads, 0, s>>>(d_plans, seeds_a, pid_a, &ctl->nseeds_raw, seeds_b, pid_b,
+                                                     &ctl->nseeds, seeds_c, pid_c, ntest);
+    k_seed_overlap<false, true><<<sms * 8, kSeedThreads, 0, s>>>(G, 0, seeds_c, ntest, seeds_b, nraw,
+                                                                  &ctl->nseeds, &ctl->bytes_overlap, d_plans,
+                                                                  pid_c, pid_b);
+    launches += 2;
     seeds = seeds_b;
     seed_pid = pid_b;
     nseeds = &ctl->nseeds;
