@@ -306,6 +306,111 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
   }
 }
 
+// The same reorder-then-write pass for rows of W words (2..8), staged as
+// plain words: tiles of 1,024 rows up to four words, 512 rows above.
+template <int W>
+__global__ void __launch_bounds__(kSortThreads)
+k_scatter_staged(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nrows, int64_t per_block,
+                 KeySpec ks, const uint32_t *__restrict__ starts, int grid) {
+  constexpr int kIt = W <= 4 ? kItems : kItems / 2;
+  constexpr int kT = kSortThreads * kIt;
+  __shared__ uint32_t s_base[kRadix];
+  __shared__ uint16_t s_cnt[kSortWarps][kRadix];
+  __shared__ uint16_t s_first[kRadix];
+  __shared__ uint16_t s_num[kRadix];
+  __shared__ int32_t s_rows[kT * W];
+  __shared__ uint16_t s_dig[kT];
+  __shared__ uint32_t s_wsum[kSortWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    s_base[d] = starts[(int64_t)d * grid + blockIdx.x];
+  const int64_t lo = (int64_t)blockIdx.x * per_block;
+  const int64_t hi = min(nrows, lo + per_block);
+  const uint32_t lt = lanemask_lt();
+  for (int64_t tile = lo; tile < hi; tile += kT) {
+    const int tn = (int)min((int64_t)kT, hi - tile);
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t dig[kIt], rank[kIt];
+#pragma unroll
+    for (int r = 0; r < kIt; ++r) {
+      const int li = warp * 32 * kIt + r * 32 + lane;
+      const bool valid = li < tn;
+      const uint32_t d = valid ? digit_of(in + (tile + li) * W, ks) : kRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t prev = 0;
+      if (valid && lane == leader) {
+        prev = s_cnt[warp][d];
+        s_cnt[warp][d] = (uint16_t)(prev + __popc(peers));
+      }
+      prev = __shfl_sync(0xffffffffu, prev, leader);
+      dig[r] = d;
+      rank[r] = prev + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t t = s_cnt[w][d];
+        s_cnt[w][d] = (uint16_t)acc;
+        acc += t;
+      }
+      s_num[d] = (uint16_t)acc;
+    }
+    __syncthreads();
+    {
+      constexpr int kPer = kRadix / kSortThreads;
+      uint32_t v[kPer], sum = 0;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        v[t] = s_num[threadIdx.x * kPer + t];
+        sum += v[t];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      uint32_t before = x - sum;
+      for (int w = 0; w < warp; ++w) before += s_wsum[w];
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        s_first[threadIdx.x * kPer + t] = (uint16_t)before;
+        before += v[t];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kIt; ++r) {
+      const int li = warp * 32 * kIt + r * 32 + lane;
+      if (li < tn) {
+        const uint32_t d = dig[r];
+        const int lp = s_first[d] + s_cnt[warp][d] + rank[r];
+        const int32_t *src = in + (tile + li) * W;
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_rows[lp * W + w] = src[w];
+        s_dig[lp] = (uint16_t)d;
+      }
+    }
+    __syncthreads();
+    // word by word, so consecutive threads write consecutive words of each run
+    for (int e = threadIdx.x; e < tn * W; e += blockDim.x) {
+      const int t = e / W, w = e - t * W;
+      const uint32_t d = s_dig[t];
+      out[((int64_t)s_base[d] + (t - s_first[d])) * W + w] = s_rows[e];
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) s_base[d] += s_num[d];
+    __syncthreads();
+  }
+}
+
 template <int W>
 void launch_scatter(const int32_t *in, int32_t *out, int64_t nrows, int64_t per_block, KeySpec ks,
                     const uint32_t *starts, int grid, cudaStream_t s) {
@@ -314,6 +419,8 @@ void launch_scatter(const int32_t *in, int32_t *out, int64_t nrows, int64_t per_
   if (W == 4 && aligned)
     k_scatter4<<<grid, kSortThreads, 0, s>>>(reinterpret_cast<const int4 *>(in), reinterpret_cast<int4 *>(out),
                                              nrows, per_block, ks, starts, grid);
+  else if constexpr (W >= 2 && W <= 8)
+    k_scatter_staged<W><<<grid, kSortThreads, 0, s>>>(in, out, nrows, per_block, ks, starts, grid);
   else
     k_scatter<W><<<grid, kSortThreads, 0, s>>>(in, out, nrows, per_block, ks, starts, grid);
 }
