@@ -244,3 +244,48 @@ def test_oracle_rejects_non_simple_targets():
         oracle.OracleGraph(3, [0, 1], [0, 2], [0, 0, 0], [0, 0])        # self-loop
     with pytest.raises(ValueError):
         oracle.OracleGraph(3, [0, 0], [1, 1], [0, 0, 0], [0, 1])        # duplicate arc
+
+
+def _induced_subpattern(g, rng, k):
+    """The induced subgraph on k vertices of g reached by a randomized search: a
+    pattern with at least one induced match (itself)."""
+    adj = {v: set() for v in range(g.n)}
+    for a, b in zip(g.src, g.dst):
+        adj[int(a)].add(int(b))
+        adj[int(b)].add(int(a))
+    for _ in range(100):
+        seen = [int(rng.integers(0, g.n))]
+        while len(seen) < k:
+            frontier = sorted({w for v in seen for w in adj[v]} - set(seen))
+            if not frontier:
+                break
+            seen.append(int(rng.choice(frontier)))
+        if len(seen) == k:
+            break
+    idx = {v: i for i, v in enumerate(seen)}
+    src, dst, elab = [], [], []
+    for a, b, l in zip(g.src, g.dst, g.elab):
+        if int(a) in idx and int(b) in idx:
+            src.append(idx[int(a)])
+            dst.append(idx[int(b)])
+            elab.append(int(l))
+    return synth.Pattern(k, np.array(src, np.int32), np.array(dst, np.int32),
+                         np.array([g.vlab[v] for v in seen], np.int32), np.array(elab, np.int32), f"sub{k}")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_oracle_equals_bruteforce_larger_patterns(seed):
+    """Patterns of 5 and 6 vertices (the GPU path is compared with the oracle up to 20),
+    taken as induced subgraphs of the target so that both modes have matches."""
+    rng = np.random.default_rng(2000 + seed)
+    g = synth.small_random_graph(7, p=float(rng.uniform(0.3, 0.6)), n_vlab=1 + seed % 2, n_elab=1 + seed % 3 // 2,
+                                 seed=50 + seed, recip=0.5, hub=bool(seed % 2))
+    og = oracle.OracleGraph.from_synth(g)
+    for k in (5, 6):
+        p = _induced_subpattern(g, rng, k)
+        for mode in (oracle.MONO, oracle.INDUCED):
+            want = bruteforce.matches_of(g, p, induced=bool(mode))
+            assert want.shape[0] >= 1
+            cnt, rows = og.match(p, mode, threads=2)
+            assert cnt == want.shape[0]
+            np.testing.assert_array_equal(rows, want)
