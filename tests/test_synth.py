@@ -62,3 +62,24 @@ def test_chung_lu_sizes_and_reciprocity(recip):
     g2 = synth.chung_lu_graph(4000, 2.1, 10, 600, n_unique, recip, synth.CELL_TYPE_WEIGHTS, 3, seed=1)
     np.testing.assert_array_equal(g.src, g2.src)
     np.testing.assert_array_equal(g.elab, g2.elab)
+
+
+def test_pattern_recipes():
+    b = synth.config4_patterns()
+    assert len(b) == 256
+    assert {p.k for p in b} <= set(range(3, 7)) and len({p.k for p in b}) == 4
+    for p in b:
+        assert synth._weakly_connected(p.k, p.src, p.dst)
+        assert p.vlab.max() < 8 and (p.elab.max() < 4 if p.mp else True)
+        pairs = set(zip(p.src.tolist(), p.dst.tolist()))
+        assert len(pairs) == p.mp and all(a != c for a, c in pairs)   # simple
+    c = synth.config3_patterns()
+    assert len(c) == 5 and all(p.k == 5 and 10 <= p.mp <= 16 for p in c)
+    arr = synth.config5_arrivals(100.0, 50)
+    times = [t for t, _, _ in arr]
+    assert all(b2 > a2 for a2, b2 in zip(times, times[1:]))
+    assert {m for _, _, m in arr} == {0, 1}
+    assert all(3 <= p.k <= 7 and synth._weakly_connected(p.k, p.src, p.dst) for _, p, _ in arr)
+    m = synth.config2_patterns()
+    assert [p.name for p in m] == ["ffl_out", "bifan", "cycle4"]
+    assert all(p.k == 4 and p.mp == 4 and p.vlab.tolist() == [0, 1, 0, 1] for p in m)
