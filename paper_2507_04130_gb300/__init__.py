@@ -52,6 +52,27 @@ def _ptr(a) -> ctypes.c_void_p:
     return ctypes.c_void_p(a.ctypes.data)
 
 
+def _check_lengths(what: str, arrays, sizes):
+    """The library reads exactly these many elements from each array."""
+    for name, a, want in zip(("src", "dst", "vlab", "elab"), arrays, sizes):
+        if int(a.shape[0]) != int(want):
+            raise ValueError(f"{what}: {name} has {int(a.shape[0])} entries, expected {int(want)}")
+
+
+def _rows_capacity(out: torch.Tensor, k: int, capacity) -> int:
+    """Rows that `out` can take; the library writes up to capacity * k int32 there on the device."""
+    if not isinstance(out, torch.Tensor) or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor")
+    if out.dtype != torch.int32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int32 tensor")
+    have = int(out.numel() // k)
+    if capacity is None:
+        return have
+    if not 0 <= int(capacity) <= have:
+        raise ValueError(f"capacity {int(capacity)} exceeds the {have} rows that out holds")
+    return int(capacity)
+
+
 class Graph:
     """A target graph resident in device memory (CSR + CSC + labels), built on the GPU.
 
@@ -67,8 +88,7 @@ class Graph:
         else:
             keep = [_host_i32(a) for a in arrays]
         m = int(keep[0].shape[0])
-        if int(keep[1].shape[0]) != m or int(keep[3].shape[0]) != m or int(keep[2].shape[0]) != n:
-            raise ValueError("array sizes do not match n and m")
+        _check_lengths("Graph", keep, (m, m, n, m))
         h = ctypes.c_void_p()
         st = lib.hm_load_graph(int(n), m, *[_ptr(a) for a in keep], 1 if on_dev else 0,
                                _stream_ptr(stream), ctypes.byref(h))
@@ -82,6 +102,7 @@ class Graph:
         vp = np.ascontiguousarray(np.asarray(vprops, dtype=np.int32).reshape(n, -1))
         keep = [_host_i32(src), _host_i32(dst)]
         m = int(keep[0].shape[0])
+        _check_lengths("Graph.with_properties", keep, (m, m))
         ep = np.ascontiguousarray(np.asarray(eprops, dtype=np.int32).reshape(m, -1))
         h = ctypes.c_void_p()
         check(lib.hm_load_graph_props(int(n), m, _ptr(keep[0]), _ptr(keep[1]), vp.shape[1], _ptr(vp),
@@ -139,6 +160,8 @@ class Pattern:
     def __init__(self, k: int, src, dst, vlab, elab, order=None):
         """`order` (optional): the original vertex at each position, replacing Alg. 1's order."""
         keep = [_host_i32(a) for a in (src, dst, vlab, elab)]
+        mp = int(keep[0].shape[0])
+        _check_lengths("Pattern", keep, (mp, mp, k, mp))
         h = ctypes.c_void_p()
         if order is None:
             st = lib.hm_load_pattern(int(k), int(keep[0].shape[0]), *[_ptr(a) for a in keep],
@@ -163,6 +186,7 @@ class Pattern:
         """A pattern whose vertices / arcs carry g's property tuples ([k, nvp], [mp, nep])."""
         keep = [_host_i32(src), _host_i32(dst)]
         mp = int(keep[0].shape[0])
+        _check_lengths("Pattern.with_properties", keep, (mp, mp))
         vp = np.ascontiguousarray(np.asarray(vprops, dtype=np.int32).reshape(k, -1))
         ep = np.ascontiguousarray(np.asarray(eprops, dtype=np.int32).reshape(mp, -1))
         h = ctypes.c_void_p()
@@ -215,9 +239,11 @@ def enumerate_matches(g: Graph, p: Pattern, mode: int, out: torch.Tensor | None 
     own = out is None
     if own:
         cap = int(capacity if capacity is not None else 1 << 20)
+        if cap < 0:
+            raise ValueError("capacity must be >= 0")
         out = torch.empty(max(cap, 1) * k, dtype=torch.int32, device="cuda")
     else:
-        cap = int(out.numel() // k) if capacity is None else int(capacity)
+        cap = _rows_capacity(out, k, capacity)
     c = ctypes.c_uint64()
     st = lib.hm_enumerate_matches(g.handle, p.handle, int(mode), ctypes.c_void_p(out.data_ptr()),
                                   cap, ctypes.byref(c), _stream_ptr(stream))
@@ -242,9 +268,10 @@ def enumerate_matches_part(g: Graph, p: Pattern, mode: int, part: int, nparts: i
                            out: torch.Tensor, stream=None) -> torch.Tensor:
     """Rows of the matches seeded by one arc range, written to `out` (sorted); raises on capacity."""
     k = p.k
+    cap = _rows_capacity(out, k, None)
     c = ctypes.c_uint64()
     check(lib.hm_enumerate_matches_part(g.handle, p.handle, int(mode), int(part), int(nparts),
-                                        ctypes.c_void_p(out.data_ptr()), int(out.numel() // k),
+                                        ctypes.c_void_p(out.data_ptr()), cap,
                                         ctypes.byref(c), _stream_ptr(stream)),
           "hm_enumerate_matches_part", int(c.value))
     return out[: int(c.value) * k].view(int(c.value), k)
@@ -318,6 +345,8 @@ class Server:
 
     def submit(self, pattern, mode: int, want_rows: bool = True) -> int:
         arrays = [_host_i32(a) for a in (pattern.src, pattern.dst, pattern.vlab, pattern.elab)]
+        mp = int(arrays[0].shape[0])
+        _check_lengths("Server.submit", arrays, (mp, mp, pattern.k, mp))
         qid = ctypes.c_uint64()
         check(lib.hm_server_submit(self._h, int(pattern.k), int(arrays[0].shape[0]), *[_ptr(a) for a in arrays],
                                    int(mode), 1 if want_rows else 0, ctypes.byref(qid)), "hm_server_submit")
@@ -373,7 +402,9 @@ def count_matches_rooted(g: Graph, p: Pattern, mode: int, root: int, mask, strea
     """Count only matches whose image of original pattern vertex `root` is flagged in mask (uint8[n])."""
     if not (isinstance(mask, torch.Tensor) and mask.is_cuda):
         mask = torch.as_tensor(np.asarray(mask, dtype=np.uint8)).cuda()
-    mask = mask.to(torch.uint8).contiguous()
+    mask = mask.to(torch.uint8).contiguous().reshape(-1)
+    if int(mask.numel()) != g.n:
+        raise ValueError(f"mask has {int(mask.numel())} entries, the graph {g.n} vertices")
     c = ctypes.c_uint64()
     check(lib.hm_count_matches_rooted(g.handle, p.handle, int(mode), int(root),
                                       ctypes.c_void_p(mask.data_ptr()), ctypes.byref(c),

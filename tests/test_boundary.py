@@ -3,7 +3,9 @@
   * the library loads and exports every function include/hipermotif.h declares;
   * hm_load_pattern validates patterns and runs Alg. 1 exactly like the
     oracle's plain restatement (hand-worked cases and random patterns);
-  * loading a graph without a device fails with a status, not a crash.
+  * loading a graph without a device fails with a status, not a crash;
+  * the Python front end rejects arrays of the wrong length and unusable row
+    buffers before it calls the library (the CUDA-tensor cases are marked gpu).
 """
 from __future__ import annotations
 
@@ -156,3 +158,44 @@ def test_pattern_with_a_given_order(hm):
     with pytest.raises(hm.HMError) as ei:                       # not a permutation
         hm.Pattern.from_synth(p, order=[0, 1, 1])
     assert ei.value.status == hm.binding.HM_ERR_ARG
+
+
+def test_pattern_arrays_must_have_the_declared_lengths(hm):
+    with pytest.raises(ValueError, match="vlab"):
+        hm.Pattern(3, [0, 1], [1, 2], [0, 0], [0, 0])          # vlab short of k
+    with pytest.raises(ValueError, match="dst"):
+        hm.Pattern(3, [0, 1], [1], [0, 0, 0], [0, 0])
+    with pytest.raises(ValueError, match="elab"):
+        hm.Pattern(3, [0, 1], [1, 2], [0, 0, 0], [0])
+
+
+class _FakeGraph:
+    handle = None
+    n = 8
+
+
+def test_row_buffers_are_checked_before_the_call(hm):
+    P = hm.Pattern(3, [0, 1], [1, 2], [0, 0, 0], [0, 0])
+    G = _FakeGraph()
+    host = torch.empty(30, dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA"):
+        hm.enumerate_matches(G, P, hm.MONO, out=host)
+    with pytest.raises(ValueError, match="CUDA"):
+        hm.enumerate_matches_part(G, P, hm.MONO, 0, 1, host)
+    with pytest.raises(ValueError, match="capacity"):
+        hm.enumerate_matches(G, P, hm.MONO, capacity=-1)
+
+
+@pytest.mark.gpu
+def test_device_row_buffers_and_masks_are_checked_before_the_call(hm):
+    P = hm.Pattern(3, [0, 1], [1, 2], [0, 0, 0], [0, 0])
+    G = _FakeGraph()                    # never reaches the library
+    dev = torch.empty(30, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError, match="exceeds"):
+        hm.enumerate_matches(G, P, hm.MONO, out=dev, capacity=11)   # 30 int32 hold 10 rows
+    with pytest.raises(ValueError, match="int32"):
+        hm.enumerate_matches(G, P, hm.MONO, out=dev.to(torch.int64))
+    with pytest.raises(ValueError, match="contiguous"):
+        hm.enumerate_matches(G, P, hm.MONO, out=dev.view(10, 3).t())
+    with pytest.raises(ValueError, match="mask"):
+        hm.count_matches_rooted(G, P, hm.MONO, 0, np.ones(G.n - 1, np.uint8))
