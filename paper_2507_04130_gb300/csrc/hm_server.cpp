@@ -87,9 +87,11 @@ void serve_slot(hm_server *S, int slot) {
     std::vector<std::shared_ptr<Query>> batch;
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      // wake for an admissible batch, or (when stopping) once nothing waits;
+      // while stopping, queries still waiting for memory are drained as usual
       S->cv.wait(lk, [&] {
-        if (S->stop) return true;
-        return !S->waiting.empty() && S->in_use + S->per_query_bytes <= S->mem_budget;
+        const bool admit = S->in_use + S->per_query_bytes <= S->mem_budget;
+        return S->stop ? (S->waiting.empty() || admit) : (!S->waiting.empty() && admit);
       });
       if (S->stop && S->waiting.empty()) break;
       while (!S->waiting.empty() && (int32_t)batch.size() < S->max_batch &&

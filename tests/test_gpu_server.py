@@ -133,3 +133,21 @@ def test_batches_overlap_on_the_device(hm):
         assert st["max_inflight_batches"] >= 2
     finally:
         srv.close()
+
+
+def test_close_drains_queries_still_waiting_for_memory(hm):
+    g = synth.er_graph(2000, 30000, 1, 1, seed=4)
+    G = hm.Graph.from_synth(g)
+    per_query = 24 * g.m + (8 << 20)
+    p = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
+                      np.zeros(3, np.int32), np.zeros(2, np.int32), "path3")
+    # three slots but memory for one query: most queries wait for memory when close() is called
+    srv = hm.Server(G, slots=3, max_batch=8, mem_budget=per_query)
+    for _ in range(12):
+        srv.submit(p, hm.MONO, want_rows=False)
+    t0 = time.perf_counter()
+    closer = threading.Thread(target=srv.close)
+    closer.start()
+    closer.join(120)
+    assert not closer.is_alive()
+    assert time.perf_counter() - t0 < 120
