@@ -113,3 +113,46 @@ def test_bfs_order_anchors_every_position(k, src, dst):
     und = {(a, b) for a, b in zip(src, dst)} | {(b, a) for a, b in zip(src, dst)}
     for i in range(1, k):
         assert any((order[i], order[j]) in und for j in range(i))
+
+
+class _FakeOracleGraph:
+    def __init__(self):
+        self.calls = []
+
+    def match(self, p, mode, rows=True, threads=1, root_mask=None):
+        self.calls.append((p.name, mode, rows, int(root_mask.sum())))
+        return 7, None
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The reference arm's JSON line: the contract's keys, values from the oracle's own timing."""
+    import json
+
+    import synth
+
+    small = synth.config2_graph(scale=8)
+    monkeypatch.setattr(synth, "cached", lambda name, fn, **kw: small)
+    og = _FakeOracleGraph()
+    monkeypatch.setattr(bench, "oracle_sample", lambda g, pats, mode, target_s: (21, 0.5, 64, 4, og))
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.main(["--impl", "reference", "--steps", "2", "--warmup", "3"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["steps"] == 2 and line["warmup"] == 3 and line["n_gpus"] == 1
+    assert line["unit"] == "matches/s" and line["higher_is_better"] is True
+    assert line["data"] == "synthetic" and "workload" in line["config"]
+    # 5 steps x 3 induced queries, every one with rows, each on its own 64-root sample
+    assert len(og.calls) == 15 and all(c[1] == 1 and c[2] and c[3] == 64 for c in og.calls)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 4 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "matches/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: pytest.fail("rank 1 ran the oracle"))
+    assert bench.main(["--impl", "reference"]) == 0
+    assert capsys.readouterr().out == ""
