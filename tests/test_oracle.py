@@ -95,6 +95,15 @@ def test_oracle_hand_worked(case):
         np.testing.assert_array_equal(got, np.array(rows, np.int32).reshape(-1, case.k))
 
 
+@pytest.mark.parametrize("case", _golden.match_cases(), ids=lambda c: c.name)
+def test_bruteforce_hand_worked(case):
+    """The brute force agrees with the hand-derived fixtures too (it pins the oracle elsewhere)."""
+    for mode_name, (count, rows) in case.expect.items():
+        got = np.asarray(bruteforce.matches_of(case.graph(), case.pattern(), MODES[mode_name]))
+        np.testing.assert_array_equal(got.reshape(-1, case.k), np.array(rows, np.int32).reshape(-1, case.k))
+        assert got.reshape(-1, case.k).shape[0] == count
+
+
 # ---------------------------------------------------------------------------
 # closed forms
 # ---------------------------------------------------------------------------
