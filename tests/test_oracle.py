@@ -225,6 +225,30 @@ def test_mono_equals_sum_of_induced_completions(seed):
     assert total > 0
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_mono_rows_are_the_disjoint_union_of_induced_completions_k4(seed):
+    """Each monomorphism is an induced match of exactly one completion (the one
+    that adds the target arcs, with their labels, among the images), so the
+    mono rows are the disjoint union of the completions' induced rows."""
+    rng = np.random.default_rng(600 + seed)
+    g = synth.small_random_graph(14, 0.35, 2, 1, seed=70 + seed, recip=0.4, hub=True)
+    og = oracle.OracleGraph.from_synth(g)
+    k = 4
+    p = synth.random_pattern(rng, k, 0.3, n_vlab=2, n_elab=1)
+    have = {(int(a), int(b)) for a, b in zip(p.src, p.dst)}
+    holes = [(a, b) for a in range(k) for b in range(k) if a != b and (a, b) not in have]
+    parts = []
+    for choice in itertools.product((0, 1), repeat=len(holes)):
+        arcs = list(zip(p.src.tolist(), p.dst.tolist())) + [h for h, c in zip(holes, choice) if c]
+        labs = p.elab.tolist() + [0] * sum(choice)
+        parts.append(og.match(_pat(k, arcs, p.vlab, labs), oracle.INDUCED)[1])
+    union = np.concatenate(parts).reshape(-1, k)
+    mono_c, mono_r = og.match(p, oracle.MONO)
+    assert union.shape[0] == mono_c > 0                       # disjoint: no row counted twice
+    order = np.lexsort(union.T[::-1])
+    np.testing.assert_array_equal(union[order], mono_r)
+
+
 # ---------------------------------------------------------------------------
 # oracle-side sanity: threads and root restriction do not change results
 # ---------------------------------------------------------------------------
