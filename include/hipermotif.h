@@ -401,12 +401,11 @@ hm_status hm_get_tuning(hm_tuning *t);
 
 /* hm_autotune -- picks the knobs above for a workload: it times the batched
  * count (hm_count_batch) of the given patterns under candidate settings
- * (leaf flattening on/off, arc filter on/off, blocks per SM 4/5, split threshold 64/512, pair
- * mode 0/1, poll interval 32/128/512, seeds per fetch 1/2, and the current
- * setting), best of two runs
- * each, until budget_ms of wall time is spent (0 = try all), installs the
- * fastest with hm_set_tuning and returns it in *best (and its time in
- * *best_ms, may be NULL).  Every run's counts are compared with the first
+ * (leaf flattening on/off, arc filter on/off, blocks per SM 4/5, split
+ * threshold 64/512, pair mode 0/1, poll interval 32/128/512, seeds per fetch
+ * 1/2, and the current setting), best of two runs each, until budget_ms of
+ * wall time is spent (0 = try all), installs the fastest with hm_set_tuning
+ * and returns it in *best (and its time in *best_ms, may be NULL).  Every run's counts are compared with the first
  * run's; a difference (which no knob can cause) restores the previous
  * setting and returns HM_ERR_CUDA.  Synchronous. */
 hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *patterns, const int32_t *modes,
