@@ -83,3 +83,24 @@ def test_pattern_recipes():
     m = synth.config2_patterns()
     assert [p.name for p in m] == ["ffl_out", "bifan", "cycle4"]
     assert all(p.k == 4 and p.mp == 4 and p.vlab.tolist() == [0, 1, 0, 1] for p in m)
+
+
+def test_cache_round_trip_and_version_key(tmp_path, monkeypatch):
+    monkeypatch.setenv("HM_CACHE", str(tmp_path))
+    calls = []
+
+    def gen(n, m, seed=0):
+        calls.append(seed)
+        return synth.er_graph(n, m, 2, 2, seed=seed)
+
+    g1 = synth.cached("er", gen, 50, 300, seed=4)
+    g2 = synth.cached("er", gen, 50, 300, seed=4)          # from the file
+    assert calls == [4]
+    for a in ("src", "dst", "vlab", "elab"):
+        np.testing.assert_array_equal(getattr(g1, a), getattr(g2, a))
+    assert g2.n == g1.n and g2.src.dtype == np.int32
+    synth.cached("er", gen, 50, 300, seed=5)               # other arguments: generated again
+    monkeypatch.setattr(synth, "_GENERATOR_VERSION", synth._GENERATOR_VERSION + 1)
+    synth.cached("er", gen, 50, 300, seed=4)               # a new generator version: not reused
+    assert calls == [4, 5, 4]
+    assert not [p for p in tmp_path.iterdir() if ".tmp" in p.name]
