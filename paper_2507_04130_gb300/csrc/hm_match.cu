@@ -142,9 +142,10 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   }
 
   // Shared position-0 states: group the seeds by their position-0 image.
-  // Monomorphism only: in induced mode the non-arcs between position 1 and
-  // the later positions prune each seed's search early, which measured faster
-  // than checking every (match, image) pair at the end.
+  // Monomorphism only: for induced calls the per-seed search measured faster
+  // than the shared one (whose (match, image) pairs are checked at the leaf by
+  // the group's warp alone), although the shared one examines far fewer
+  // candidates.
   const hm_tuning tu = tuning();
   const bool share = p->k > 2 && plan.defer1 && !plan.induced && tu.share_seeds > 0;
   const int4 *groups = nullptr;
