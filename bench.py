@@ -86,9 +86,10 @@ def hbm_peak():
 
 
 def kernel_source_hash():
-    """Hash of the sources that define k_extend (its header and the shared device helpers)."""
+    """Hash of the sources that define k_extend's launches: its header, the shared device
+    helpers, and the single-pattern orchestration that picks the variant and its states."""
     h = hashlib.sha256()
-    for name in ("hm_kernels.cuh", "hm_internal.cuh"):
+    for name in ("hm_kernels.cuh", "hm_internal.cuh", "hm_match.cu"):
         with open(os.path.join(ROOT, "paper_2507_04130_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

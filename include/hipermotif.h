@@ -376,13 +376,15 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      hash table, instead of a binary search (default 1;
  *                      -1: always binary search).
  *   share_seeds        1 (default): when no later pattern position has an arc
- *                      to position 1, single-pattern monomorphism calls group
- *                      the injected depth-2 states by their position-0 image,
- *                      search the other positions once per image and choose
- *                      position 1 last from the group's seeds (same result
- *                      set, far less work when hubs carry many seeds); -1: one
- *                      search per depth-2 state.  Induced calls always search
- *                      per state.
+ *                      to position 1, single-pattern calls group the injected
+ *                      depth-2 states by their position-0 image, search the
+ *                      other positions once per group and choose position 1
+ *                      last from the group's seeds, checking the induced
+ *                      non-arcs to position 1 there (same result set, far
+ *                      less work when hubs carry many seeds); induced calls
+ *                      split an image's seeds into groups of at most 32, so
+ *                      each group's warp checks few (match, seed) pairs; -1:
+ *                      one search per depth-2 state.
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {

@@ -28,8 +28,9 @@
 //                   donation requests; a busy warp claims one and splits off
 //                   half of its shallowest unfinished range through a bounded
 //                   lock-free queue.  Every wait is bounded by the call's time
-//                   budget.  For monomorphism with a pendant position 1 the
-//                   seeds of one position-0 image share one search
+//                   budget.  With a pendant position 1 the seeds of one
+//                   position-0 image (induced: at most 32 of them) share one
+//                   search, and position 1 is chosen at the leaves
 //                   (expand_position1).
 //   k_seed_rows     two-vertex patterns: each seed is already a match.
 //

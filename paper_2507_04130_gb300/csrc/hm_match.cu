@@ -32,11 +32,21 @@ Plan shared_plan(const Plan &P) {
   return Q;
 }
 
-// Seeds sorted by (u, v): flag the first seed of each position-0 image.
-__global__ void k_seed_group_flags(const int2 *__restrict__ s, int64_t n, uint32_t *__restrict__ flag) {
+// Seeds sorted by (u, v): flag the first seed of each position-0 image, and
+// (cap > 0) every seed at a multiple of `cap`, so no group holds more than
+// cap seeds.  The groups still partition the seeds.
+__global__ void k_seed_group_flags(const int2 *__restrict__ s, int64_t n, int64_t cap,
+                                   uint32_t *__restrict__ flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = i < n && (i == 0 || s[i].x != s[i - 1].x) ? 1u : 0u;
+    flag[i] = i < n && (i == 0 || s[i].x != s[i - 1].x || (cap > 0 && i % cap == 0)) ? 1u : 0u;
 }
+
+// Seeds per shared group in induced calls: each group's (match, image) pairs
+// are checked by its own warp at the leaf, so a hub's hundreds of seeds are
+// split into groups of this size, which keeps that loop short while the
+// search over the later positions still runs once per 32 seeds instead of
+// once per seed.
+constexpr int64_t kInducedGroupCap = 32;
 
 // One int4 {u, first, end, 0} per group; idx is the exclusive scan of flag.
 __global__ void k_seed_groups(const int2 *__restrict__ s, int64_t n, const uint32_t *__restrict__ flag,
@@ -141,13 +151,10 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     return HM_OK;
   }
 
-  // Shared position-0 states: group the seeds by their position-0 image.
-  // Monomorphism only: for induced calls the per-seed search measured faster
-  // than the shared one (whose (match, image) pairs are checked at the leaf by
-  // the group's warp alone), although the shared one examines far fewer
-  // candidates.
+  // Shared position-0 states: group the seeds by their position-0 image
+  // (induced calls: at most kInducedGroupCap seeds per group).
   const hm_tuning tu = tuning();
-  const bool share = p->k > 2 && plan.defer1 && !plan.induced && tu.share_seeds > 0;
+  const bool share = p->k > 2 && plan.defer1 && tu.share_seeds > 0;
   const int4 *groups = nullptr;
   Timer t_grp(s, timing && share);
   if (share) {
@@ -170,7 +177,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
       if (r != HM_OK) return r;
       launches += radix_sort_launches(2 * bits_for(g->n));
       const int gb = (int)std::min<unsigned long long>((ns + 256) / 256, (unsigned long long)sms * 8);
-      k_seed_group_flags<<<gb, 256, 0, s>>>(seeds, (int64_t)ns, flag);
+      k_seed_group_flags<<<gb, 256, 0, s>>>(seeds, (int64_t)ns, plan.induced ? kInducedGroupCap : 0, flag);
       r = exclusive_scan_u32(flag, idx, (int64_t)ns + 1, s);
       if (r != HM_OK) return r;
       k_seed_groups<<<gb, 256, 0, s>>>(seeds, (int64_t)ns, flag, idx, gr, &ctl->ngroups);

@@ -76,6 +76,7 @@ def _fake_tree(tmp_path, kernels_text, profile_hash, per_launch="6.2e9"):
     csrc.mkdir(parents=True)
     (csrc / "hm_kernels.cuh").write_text(kernels_text)
     (csrc / "hm_internal.cuh").write_text("// helpers\n")
+    (csrc / "hm_match.cu").write_text("// orchestration\n")
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "k_extend_rmat20.md").write_text(
