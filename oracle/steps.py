@@ -213,13 +213,28 @@ def edge_validator(T: TargetLists, vlab, P: ReorderedPattern, induced: bool,
         if induced and fwd is not None:             # R7
             return None
     # degree thresholds for position 1
-    if T.indeg(v) < P.indeg[1] or T.outdeg(v) < P.outdeg[1]:
+    if not position1_degrees_ok(T, P, v):
         return None
     # neighbour overlap (R8)
-    need = len(P.nbhd(0) & P.nbhd(1))
-    if need > 0 and len(T.nbhd(u) & T.nbhd(v)) < need:
+    if not overlap_ok(T, P, u, v):
         return None
     return (int(u), int(v))
+
+
+def position1_degrees_ok(T: TargetLists, P: ReorderedPattern, v: int) -> bool:
+    """Alg. 3's degree test on the image of position 1: in- and out-degree at least the pattern's."""
+    return T.indeg(v) >= P.indeg[1] and T.outdeg(v) >= P.outdeg[1]
+
+
+def neighbour_overlap(T: TargetLists, u: int, v: int) -> int:
+    """|N_u & N_v|, N_x the set of in- and out-neighbours of x, each counted once (R8)."""
+    return len(T.nbhd(u) & T.nbhd(v))
+
+
+def overlap_ok(T: TargetLists, P: ReorderedPattern, u: int, v: int) -> bool:
+    """Alg. 3's neighbour-overlap test |N_u & N_v| >= |N_0 & N_1|, skipped when the right side is 0."""
+    need = len(P.nbhd(0) & P.nbhd(1))
+    return need == 0 or neighbour_overlap(T, u, v) >= need
 
 
 def injected_states(graph, pattern, induced: bool) -> np.ndarray:

@@ -441,8 +441,11 @@ _GENERATOR_VERSION = 2
 
 
 def cached(name: str, fn, *args, **kwargs) -> Graph:
-    """Return fn(*args, **kwargs), memoised as an .npz under $HM_CACHE (default /tmp/hm_cache)."""
-    root = os.environ.get("HM_CACHE", "/tmp/hm_cache")
+    """Return fn(*args, **kwargs), memoised as an .npz under $HM_CACHE (default: the user's
+    cache directory, $XDG_CACHE_HOME or ~/.cache, subfolder hipermotif_synth)."""
+    root = os.environ.get("HM_CACHE") or os.path.join(
+        os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache"),
+        "hipermotif_synth")
     os.makedirs(root, exist_ok=True)
     key = f"{name}_v{_GENERATOR_VERSION}_" + "_".join(str(a) for a in args) + "_" + "_".join(
         f"{k}{v}" for k, v in sorted(kwargs.items()))

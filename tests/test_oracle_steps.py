@@ -8,6 +8,13 @@
     completeness theorem for state injection): for every match the oracle
     finds, the pair (f(pos0), f(pos1)) is among the injected states; and every
     injected state is a genuine partial match of positions 0 and 1.
+  * Alg. 3's pruning thresholds, which soundness alone cannot pin (a reading
+    that under-prunes stays sound): hand-worked injected states
+    (tests/golden/states_by_hand.txt) in which the position-1 degree threshold,
+    or the neighbour-overlap threshold |N_u & N_v| >= |N_0 & N_1| (R8), alone
+    rejects an arc; every planted misreading of either threshold (dropped,
+    degrees swapped, only out- or only in-neighbours, a reciprocal neighbour
+    counted twice, ">" for ">=") fails one of them.
 """
 from __future__ import annotations
 
@@ -109,3 +116,81 @@ def test_reversed_seed_direction():
     # target arc 1->0 seeds f(pos0)=0, f(pos1)=1; arc 2->0 seeds (0, 2)
     got = steps.injected_states(g, p, induced=False)
     np.testing.assert_array_equal(got, [[0, 1], [0, 2]])
+
+
+# ---------------------------------------------------------------------------
+# hand-worked injected states (tests/golden/states_by_hand.txt): the
+# position-1 degree threshold and the neighbour-overlap threshold of Alg. 3
+# each decide some arc on their own
+# ---------------------------------------------------------------------------
+
+_STATE_CASES = _golden.match_cases("states_by_hand.txt")
+
+
+@pytest.mark.parametrize("mode", ["mono", "induced"])
+@pytest.mark.parametrize("case", _STATE_CASES, ids=lambda c: c.name)
+def test_injected_states_hand_worked(case, mode):
+    want = np.array(case.expect[mode][1], np.int32).reshape(-1, 2)
+    got = steps.injected_states(case.graph(), case.pattern(), mode == "induced")
+    np.testing.assert_array_equal(got, want)
+
+
+def _fixtures_pass() -> bool:
+    for case in _STATE_CASES:
+        for mode in ("mono", "induced"):
+            want = np.array(case.expect[mode][1], np.int32).reshape(-1, 2)
+            got = steps.injected_states(case.graph(), case.pattern(), mode == "induced")
+            if not np.array_equal(got, want):
+                return False
+    return True
+
+
+def _overlap_out_only(T, u, v):
+    return len(set(T.outs(u).tolist()) & set(T.outs(v).tolist()))
+
+
+def _overlap_in_only(T, u, v):
+    return len(set(T.ins(u).tolist()) & set(T.ins(v).tolist()))
+
+
+def _overlap_repeats_counted(T, u, v):
+    # walks u's out-list and then its in-list, so a reciprocal neighbour counts twice
+    nv = T.nbhd(v)
+    return sum(1 for w in list(T.outs(u)) + list(T.ins(u)) if int(w) in nv)
+
+
+def _overlap_strict(T, P, u, v):
+    need = len(P.nbhd(0) & P.nbhd(1))
+    return need == 0 or steps.neighbour_overlap(T, u, v) > need
+
+
+def _degrees_swapped(T, P, v):
+    return T.indeg(v) >= P.outdeg[1] and T.outdeg(v) >= P.indeg[1]
+
+
+def _degrees_out_only(T, P, v):
+    return T.outdeg(v) >= P.outdeg[1]
+
+
+VALIDATOR_MISTAKES = {
+    "drop_position1_degrees": ("position1_degrees_ok", lambda T, P, v: True),
+    "position1_degrees_swapped": ("position1_degrees_ok", _degrees_swapped),
+    "position1_out_degree_only": ("position1_degrees_ok", _degrees_out_only),
+    "drop_overlap": ("overlap_ok", lambda T, P, u, v: True),
+    "overlap_strictly_greater": ("overlap_ok", _overlap_strict),
+    "overlap_out_neighbours_only": ("neighbour_overlap", _overlap_out_only),
+    "overlap_in_neighbours_only": ("neighbour_overlap", _overlap_in_only),
+    "overlap_counts_repeats": ("neighbour_overlap", _overlap_repeats_counted),
+}
+
+
+def test_unmutated_validator_passes_fixtures():
+    assert _fixtures_pass()
+
+
+@pytest.mark.parametrize("name", sorted(VALIDATOR_MISTAKES))
+def test_planted_validator_mistake_is_caught(monkeypatch, name):
+    """Each plausible misreading of Alg. 3's two thresholds fails a hand-worked fixture."""
+    attr, wrong = VALIDATOR_MISTAKES[name]
+    monkeypatch.setattr(steps, attr, wrong)
+    assert not _fixtures_pass()
