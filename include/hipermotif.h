@@ -183,6 +183,14 @@ void hm_free_pattern(hm_pattern *p);
  * original pattern vertex placed at position i.  Host-only. */
 hm_status hm_pattern_order(const hm_pattern *p, int32_t *order_out);
 
+/* hm_pattern_automorphisms -- the number of label-preserving automorphisms of
+ * the pattern that its search uses for symmetry breaking (the matches of
+ * Sec. II-A come in orbits of this size; see hm_tuning.symmetry): the order of
+ * the automorphism group when it is between 2 and 64, else 1 (the group is
+ * trivial, too large, or the pattern has two vertices).  Host only.
+ *   count HOST output. */
+hm_status hm_pattern_automorphisms(const hm_pattern *p, int32_t *count);
+
 /* ------------------------------------------------------------------------
  * Matching.
  *
@@ -325,10 +333,17 @@ hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, hm_mode mod
  *   The first call on a device looks up the array's device address (with that
  *   device current) and caches it; make that first call before any stream
  *   capture.  The call allocates nothing: no cudaMalloc, no cudaFree, no pool.
+ *   Every call copies its control block back and synchronises `stream` before
+ *   it returns, so the host waits for the count.
  *   All calls on a device share the array, which keeps the previous call's
  *   contents (the call clears what must start at zero): calls whose work
  *   overlaps on the GPU, e.g. on two streams, race on it -- serialise them.
- *   Otherwise as hm_count_matches (same result, same errors). */
+ *   Otherwise as hm_count_matches (same result, same errors), with one
+ *   difference in speed: it does not group depth-2 states by their position-0
+ *   image (hm_tuning.share_seeds), because the grouping sorts the states into
+ *   temporary buffers that the fixed array has no room for, so a pattern with
+ *   a pendant position 1 (e.g. the feed-forward loop plus out-edge) takes the
+ *   one-search-per-state path. */
 enum { HM_STATIC_SCRATCH_BYTES = 64 << 20, HM_STATIC_MAX_ARCS = 3702528 };
 
 hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern *p, hm_mode mode,
@@ -385,6 +400,24 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      split an image's seeds into groups of at most 32, so
  *                      each group's warp checks few (match, seed) pairs; -1:
  *                      one search per depth-2 state.
+ *   symmetry           1 (default): a pattern with a non-trivial group of
+ *                      label-preserving automorphisms (at most 64 of them)
+ *                      is searched for one map per orbit -- order
+ *                      constraints between symmetric positions, chosen by
+ *                      orbits and stabilisers -- and each map found is
+ *                      emitted with its automorphic images (same count and
+ *                      rows; a pattern with two automorphisms takes about
+ *                      half the search).  Not used for rooted counts, for
+ *                      two-vertex patterns or with shared position-0
+ *                      states.  -1: every map is searched for itself.
+ *   warps_per_state    1, 2 or 4: warps that share one depth-2 state.
+ *                      Each claim from the state queue is a (state, part)
+ *                      pair; the warp takes that part of the state's first
+ *                      extension range (contiguous equal slices), so a
+ *                      hub's state starts on several warps at once instead
+ *                      of waiting for donations.  0 (default): automatic --
+ *                      4 for shared position-0 states (share_seeds), 1
+ *                      otherwise.
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -396,23 +429,41 @@ typedef struct {
   int32_t leaf_flatten;
   int32_t arc_filter;
   int32_t share_seeds;
+  int32_t symmetry;
+  int32_t warps_per_state;
 } hm_tuning;
 
 hm_status hm_set_tuning(const hm_tuning *t);
 hm_status hm_get_tuning(hm_tuning *t);
 
 /* hm_autotune -- picks the knobs above for a workload: it times the batched
- * count (hm_count_batch) of the given patterns under candidate settings
- * (leaf flattening on/off, arc filter on/off, blocks per SM 4/5, split
- * threshold 64/512, pair mode 0/1, poll interval 32/128/512, seeds per fetch
- * 1/2, and the current setting), best of two runs each, until budget_ms of
- * wall time is spent (0 = try all), installs the fastest with hm_set_tuning
- * and returns it in *best (and its time in *best_ms, may be NULL).  Every run's counts are compared with the first
- * run's; a difference (which no knob can cause) restores the previous
- * setting and returns HM_ERR_CUDA.  Synchronous. */
+ * count (hm_count_batch) of the given patterns and improves the setting by
+ * coordinate descent, one knob at a time over its candidate values (warps
+ * per state 1/2/4; queue chunk, i.e. states claimed at once, 1..64; the
+ * intersection strategy arc_filter: filter probes, binary search in sorted
+ * lists of up to 16 entries, or binary search always; blocks per SM 4/5/6;
+ * split threshold 16..1024; poll interval 32/128/512; pair mode; leaf
+ * flattening), keeping a change only when it is more than 1 % faster (best of
+ * two runs each), until a pass changes nothing or budget_ms of wall time is
+ * spent (0 = no limit).  It installs the fastest setting with hm_set_tuning
+ * and returns it in *best (its time in *best_ms, may be NULL).  Every run's
+ * counts are compared with a reference run's; a difference (which no knob can
+ * cause) restores the previous setting and returns HM_ERR_CUDA.  Synchronous. */
 hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *patterns, const int32_t *modes,
                       int32_t npat, uint32_t budget_ms, hm_tuning *best, float *best_ms,
                       void *stream);
+
+/* hm_autotune_cached -- hm_autotune with a cache file (host path; NULL or ""
+ * = none).  The key is a fingerprint of the graph (its sizes and a strided
+ * sample of its sorted arc arrays) and of the workload (how many patterns of
+ * each size and mode).  A setting stored under the key is installed without
+ * timing (*from_cache = 1, *best_ms = the time stored with it); otherwise the
+ * tuner runs and appends its choice to the file as one text line
+ * "<key> name=value ... ms=<time>".  from_cache may be NULL. */
+hm_status hm_autotune_cached(const hm_graph *g, const hm_pattern *const *patterns,
+                             const int32_t *modes, int32_t npat, uint32_t budget_ms,
+                             const char *cache_path, hm_tuning *best, float *best_ms,
+                             int32_t *from_cache, void *stream);
 
 /* ------------------------------------------------------------------------
  * Statistics of the calling thread's last matching call (host struct).

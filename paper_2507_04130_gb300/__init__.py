@@ -207,6 +207,12 @@ class Pattern:
         check(lib.hm_pattern_order(self._h, _ptr(out)), "hm_pattern_order")
         return out.tolist()
 
+    def automorphisms(self) -> int:
+        """Size of the automorphism group the search uses for symmetry breaking (1: none)."""
+        c = ctypes.c_int32()
+        check(lib.hm_pattern_automorphisms(self._h, ctypes.byref(c)), "hm_pattern_automorphisms")
+        return int(c.value)
+
     def close(self):
         if getattr(self, "_h", None):
             lib.hm_free_pattern(self._h)
@@ -315,15 +321,20 @@ def enumerate_batch(g: Graph, patterns, modes, counts=None, stream=None) -> list
     return [buf[int(offs[i]): int(offs[i + 1])].view(int(got[i]), ks[i]) for i in range(n)]
 
 
-def autotune(g: Graph, patterns, modes, budget_ms: int = 2000, stream=None) -> dict:
-    """Time candidate launch knobs on the batched count of `patterns`; install and return the best."""
+def autotune(g: Graph, patterns, modes, budget_ms: int = 2000, stream=None, cache: str | None = None) -> dict:
+    """Tune the launch knobs on the batched count of `patterns` (coordinate descent); install and
+    return the best.  With `cache` (a file path), a setting stored for the same graph and pattern
+    mix is reused without timing, and a new choice is appended to the file."""
     n, handles, m = _batch_args(patterns, modes)
     t = binding.hm_tuning()
     ms = ctypes.c_float()
-    check(lib.hm_autotune(g.handle, ctypes.cast(handles, ctypes.c_void_p), _ptr(m), n, int(budget_ms),
-                          ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)), "hm_autotune")
+    hit = ctypes.c_int32()
+    check(lib.hm_autotune_cached(g.handle, ctypes.cast(handles, ctypes.c_void_p), _ptr(m), n, int(budget_ms),
+                                 cache.encode() if cache else None, ctypes.byref(t), ctypes.byref(ms),
+                                 ctypes.byref(hit), _stream_ptr(stream)), "hm_autotune_cached")
     out = t.as_dict()
     out["ms"] = float(ms.value)
+    out["from_cache"] = bool(hit.value)
     return out
 
 
@@ -437,11 +448,11 @@ def set_counters(enabled: bool):
 
 def set_tuning(extend_min_blocks: int = 0, split_min: int = 0, pair_mode: int = 0,
                seeds_per_fetch: int = 0, poll_every: int = 0, leaf_flatten: int = 0,
-               arc_filter: int = 0, share_seeds: int = 0):
+               arc_filter: int = 0, share_seeds: int = 0, symmetry: int = 0, warps_per_state: int = 0):
     """Set the extension kernel's launch knobs (0 = default; results never change)."""
     t = binding.hm_tuning(int(extend_min_blocks), int(split_min), int(pair_mode),
                           int(seeds_per_fetch), int(poll_every), int(leaf_flatten), int(arc_filter),
-                          int(share_seeds))
+                          int(share_seeds), int(symmetry), int(warps_per_state))
     check(lib.hm_set_tuning(ctypes.byref(t)), "hm_set_tuning")
 
 

@@ -28,7 +28,7 @@ EXPORTED = [
     "hm_set_tuning", "hm_get_tuning", "hm_count_batch", "hm_enumerate_batch", "hm_autotune",
     "hm_server_create", "hm_server_submit", "hm_server_poll", "hm_server_release",
     "hm_server_stats", "hm_server_destroy", "hm_load_graph_props", "hm_load_pattern_props",
-    "hm_load_pattern_ordered",
+    "hm_load_pattern_ordered", "hm_pattern_automorphisms", "hm_autotune_cached",
 ]
 
 
@@ -74,6 +74,8 @@ class hm_tuning(ctypes.Structure):
         ("leaf_flatten", ctypes.c_int32),
         ("arc_filter", ctypes.c_int32),
         ("share_seeds", ctypes.c_int32),
+        ("symmetry", ctypes.c_int32),
+        ("warps_per_state", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -126,6 +128,10 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_float), _vp]),
     "hm_enumerate_batch": (_st, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "hm_get_tuning": (_st, [ctypes.POINTER(hm_tuning)]),
+    "hm_pattern_automorphisms": (_st, [_vp, ctypes.POINTER(_i32)]),
+    "hm_autotune_cached": (_st, [_vp, _vp, _vp, _i32, ctypes.c_uint32, ctypes.c_char_p,
+                                 ctypes.POINTER(hm_tuning), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(_i32), _vp]),
 }
 
 

@@ -15,6 +15,8 @@ std::atomic<int> g_poll_every{128};
 std::atomic<int> g_leaf_flatten{1};
 std::atomic<int> g_arc_filter{kDefaultFilterMin};
 std::atomic<int> g_share_seeds{1};
+std::atomic<int> g_symmetry{1};
+std::atomic<int> g_warps_per_state{0};  // 0: automatic
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -33,6 +35,8 @@ hm_tuning tuning() {
   t.leaf_flatten = g_leaf_flatten.load(std::memory_order_relaxed);
   t.arc_filter = g_arc_filter.load(std::memory_order_relaxed);
   t.share_seeds = g_share_seeds.load(std::memory_order_relaxed);
+  t.symmetry = g_symmetry.load(std::memory_order_relaxed);
+  t.warps_per_state = g_warps_per_state.load(std::memory_order_relaxed);
   return t;
 }
 int32_t filter_min() { return g_arc_filter.load(std::memory_order_relaxed); }
@@ -87,7 +91,9 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   if ((mb != 4 && mb != 5 && mb != 6) || sm < 2 || sp < 1 || sp > 1024 ||
       (t->pair_mode != 0 && t->pair_mode != 1) || pe < 1 || pe > 65536 || (pe & (pe - 1)) ||
       t->leaf_flatten < -1 || t->leaf_flatten > 1 || t->arc_filter < -1 || t->share_seeds < -1 ||
-      t->share_seeds > 1)
+      t->share_seeds > 1 || t->symmetry < -1 || t->symmetry > 1 ||
+      (t->warps_per_state != 0 && t->warps_per_state != 1 && t->warps_per_state != 2 &&
+       t->warps_per_state != 4))
     return HM_ERR_ARG;
   hm::g_min_blocks.store(mb);
   hm::g_split_min.store(sm);
@@ -97,6 +103,8 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   hm::g_leaf_flatten.store(t->leaf_flatten < 0 ? -1 : 1);
   hm::g_arc_filter.store(t->arc_filter ? t->arc_filter : hm::kDefaultFilterMin);
   hm::g_share_seeds.store(t->share_seeds < 0 ? -1 : 1);
+  hm::g_symmetry.store(t->symmetry < 0 ? -1 : 1);
+  hm::g_warps_per_state.store(t->warps_per_state);
   return HM_OK;
 }
 

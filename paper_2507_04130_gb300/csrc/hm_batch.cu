@@ -218,6 +218,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   for (int32_t i = 0; i < npat; ++i) {
     if (!pats[i] || (modes[i] != HM_MONO && modes[i] != HM_INDUCED)) return HM_ERR_ARG;
     plans[i] = pats[i]->plan[modes[i]];
+    if (tuning().symmetry < 0) strip_symmetry(plans[i]);
     ks[i] = pats[i]->k;
     grp_slots = std::max(grp_slots, plans[i].ngrp);
     kmax = std::max(kmax, ks[i]);
@@ -364,7 +365,8 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   A.pair_mode = tu.pair_mode;
   A.seeds_per_fetch = tu.seeds_per_fetch;
   A.poll_mask = (uint32_t)tu.poll_every - 1u;
-    A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
+  A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
+  A.wps_shift = wps_shift(tu);
   A.seeds = seeds;
   A.nseeds = nseeds;
   A.qbuf = qbuf;
@@ -385,12 +387,14 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   const int slot = min_blocks_slot(tu.extend_min_blocks);
   const size_t smem = warp_smem_bytes(grp_slots) * kExtWarps;
   const bool counters = counters_enabled();
-  const int grid = extend_grid<true>(want_rows, counters, smem, slot);
+  bool sym = false;
+  for (const Plan &pl : plans) sym |= pl.naut > 1;
+  const int grid = extend_grid<true>(want_rows, counters, smem, slot, false, sym);
   if (grid <= 0) return HM_ERR_CUDA;
   st.extend_grid = grid;
   st.extend_block = kExtThreads;
   Timer t_ext(s, timing);
-  extend_kernel<true>(want_rows, counters, slot)<<<grid, kExtThreads, smem, s>>>(G, plans[0], A);
+  extend_kernel<true>(want_rows, counters, slot, false, sym)<<<grid, kExtThreads, smem, s>>>(G, plans[0], A);
   launches += 1;
   t_ext.stop();
   HM_CUDA_TRY(cudaGetLastError());
@@ -476,64 +480,230 @@ extern "C" hm_status hm_enumerate_batch(const hm_graph *g, const hm_pattern *con
 
 // ---------------------------------------------------------------------------
 // hm_autotune: pick the extension kernel's launch knobs for a workload by
-// timing candidate settings on its batched count.
+// timing candidate settings on its batched count (coordinate descent), with
+// an optional cache file of earlier choices.
 // ---------------------------------------------------------------------------
 #include <chrono>
+#include <cstdio>
+#include <string>
 
-extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *patterns,
-                                 const int32_t *modes, int32_t npat, uint32_t budget_ms,
-                                 hm_tuning *best, float *best_ms, void *stream) {
+namespace hm {
+namespace {
+
+// The knobs the tuner searches, each with its candidate values.
+struct Dim {
+  int32_t hm_tuning::*field;
+  std::vector<int32_t> values;
+};
+
+std::vector<Dim> tune_dims() {
+  return {
+      {&hm_tuning::warps_per_state, {1, 2, 4}},
+      {&hm_tuning::seeds_per_fetch, {1, 2, 4, 8, 16, 32, 64}},
+      {&hm_tuning::arc_filter, {1, 16, -1}},  // intersection: filter probe / binary search in short lists / always
+      {&hm_tuning::extend_min_blocks, {4, 5, 6}},
+      {&hm_tuning::split_min, {16, 64, 256, 1024}},
+      {&hm_tuning::poll_every, {32, 128, 512}},
+      {&hm_tuning::pair_mode, {0, 1}},
+      {&hm_tuning::leaf_flatten, {1, -1}},
+  };
+}
+
+const char *kTuneFields[] = {"extend_min_blocks", "split_min", "pair_mode", "seeds_per_fetch", "poll_every",
+                             "leaf_flatten", "arc_filter", "share_seeds", "symmetry", "warps_per_state"};
+int32_t hm_tuning::*const kTuneMembers[] = {
+    &hm_tuning::extend_min_blocks, &hm_tuning::split_min, &hm_tuning::pair_mode, &hm_tuning::seeds_per_fetch,
+    &hm_tuning::poll_every, &hm_tuning::leaf_flatten, &hm_tuning::arc_filter, &hm_tuning::share_seeds,
+    &hm_tuning::symmetry, &hm_tuning::warps_per_state};
+constexpr int kNumTuneFields = 10;
+
+// A fingerprint of the graph (sizes, directory sizes and a strided sample of
+// its sorted arc arrays, FNV-1a) and of the workload (the multiset of pattern
+// sizes and modes): the cache key of a tuned setting.
+std::string tune_key(const hm_graph *g, const hm_pattern *const *patterns, const int32_t *modes, int32_t npat,
+                     cudaStream_t s) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xff;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)g->n);
+  mix((uint64_t)g->m);
+  mix((uint64_t)g->ndir_out);
+  mix((uint64_t)g->ndir_in);
+  constexpr int kSamples = 64, kRun = 16;
+  std::vector<int32_t> buf(2 * kSamples * kRun, 0);
+  if (g->m >= kRun) {
+    for (int i = 0; i < kSamples; ++i) {
+      const int64_t at = (g->m - kRun) * i / std::max(kSamples - 1, 1);
+      cudaMemcpyAsync(buf.data() + 2 * i * kRun, g->src + at, sizeof(int32_t) * kRun, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(buf.data() + (2 * i + 1) * kRun, g->out_adj + at, sizeof(int32_t) * kRun,
+                      cudaMemcpyDeviceToHost, s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) (void)cudaGetLastError();
+  }
+  for (int32_t v : buf) mix((uint32_t)v);
+  int hist[2][HM_MAX_K + 1] = {};
+  for (int32_t i = 0; i < npat; ++i) hist[modes[i] ? 1 : 0][patterns[i]->k]++;
+  std::string key;
+  char tmp[64];
+  std::snprintf(tmp, sizeof tmp, "g%016llx", (unsigned long long)h);
+  key += tmp;
+  for (int m = 0; m < 2; ++m)
+    for (int k = 2; k <= HM_MAX_K; ++k)
+      if (hist[m][k]) {
+        std::snprintf(tmp, sizeof tmp, "_%c%dx%d", m ? 'i' : 'm', k, hist[m][k]);
+        key += tmp;
+      }
+  return key;
+}
+
+// The last line of the cache file with this key: "<key> name=value ... ms=<t>".
+bool cache_lookup(const char *path, const std::string &key, hm_tuning *t, float *ms) {
+  FILE *f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char k[256];
+    int off = 0;
+    if (std::sscanf(line, "%255s%n", k, &off) != 1 || key != k) continue;
+    hm_tuning c{};
+    float m = 0.f;
+    int got = 0;
+    const char *p = line + off;
+    char name[64];
+    double v;
+    int n = 0;
+    while (std::sscanf(p, " %63[a-z_]=%lf%n", name, &v, &n) == 2) {
+      p += n;
+      if (std::string(name) == "ms") {
+        m = (float)v;
+        continue;
+      }
+      for (int i = 0; i < kNumTuneFields; ++i)
+        if (std::string(name) == kTuneFields[i]) {
+          c.*kTuneMembers[i] = (int32_t)v;
+          ++got;
+        }
+    }
+    if (got == kNumTuneFields) {
+      *t = c;
+      *ms = m;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char *path, const std::string &key, const hm_tuning &t, float ms) {
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s", key.c_str());
+  for (int i = 0; i < kNumTuneFields; ++i) std::fprintf(f, " %s=%d", kTuneFields[i], t.*kTuneMembers[i]);
+  std::fprintf(f, " ms=%.4f\n", ms);
+  std::fclose(f);
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_autotune_cached(const hm_graph *g, const hm_pattern *const *patterns,
+                                        const int32_t *modes, int32_t npat, uint32_t budget_ms,
+                                        const char *cache_path, hm_tuning *best, float *best_ms,
+                                        int32_t *from_cache, void *stream) {
   if (!g || !best || npat <= 0 || !patterns || !modes) return HM_ERR_ARG;
+  for (int32_t i = 0; i < npat; ++i)
+    if (!patterns[i]) return HM_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (from_cache) *from_cache = 0;
   hm_tuning before{};
   hm_get_tuning(&before);
+  std::string key;
+  if (cache_path && *cache_path) {
+    key = hm::tune_key(g, patterns, modes, npat, s);
+    hm_tuning c{};
+    float ms = 0.f;
+    if (hm::cache_lookup(cache_path, key, &c, &ms) && hm_set_tuning(&c) == HM_OK) {
+      hm_get_tuning(best);
+      if (best_ms) *best_ms = ms;
+      if (from_cache) *from_cache = 1;
+      return HM_OK;
+    }
+  }
   std::vector<uint64_t> counts(npat), ref(npat);
   // reference run with the current knobs (also warms caches and the pool)
   hm_status st = hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, ref.data(), s);
   if (st != HM_OK) return st;
-  static const int32_t kMb[] = {4, 5};
-  static const int32_t kSplit[] = {64, 512};
-  static const int32_t kPair[] = {0, 1};
-  static const int32_t kPoll[] = {32, 128, 512};
-  static const int32_t kFetch[] = {1, 2};
-  static const int32_t kFlat[] = {1, -1};
-  static const int32_t kFilter[] = {1, -1};  // membership tests: filter + hash table, or binary search
-  std::vector<hm_tuning> cands;
-  cands.push_back(before);
-  for (int32_t fl : kFlat)
-    for (int32_t af : kFilter)
-      for (int32_t mb : kMb)
-        for (int32_t sp : kSplit)
-          for (int32_t pm : kPair)
-            for (int32_t po : kPoll)
-              for (int32_t fe : kFetch) cands.push_back(hm_tuning{mb, sp, pm, fe, po, fl, af, before.share_seeds});
   const auto t_start = std::chrono::steady_clock::now();
-  double best_t = 1e30;
-  hm_tuning pick = before;
-  for (const hm_tuning &c : cands) {
-    if (hm_set_tuning(&c) != HM_OK) continue;
+  auto spent_ms = [&] {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  };
+  // best of two timed runs; a count that differs from the reference (which
+  // no knob can cause) is reported as an error
+  auto measure = [&](const hm_tuning &c, double *t_out) -> hm_status {
+    hm_status r = hm_set_tuning(&c);
+    if (r != HM_OK) return r;
     double t_min = 1e30;
     for (int rep = 0; rep < 2; ++rep) {
       const auto t0 = std::chrono::steady_clock::now();
-      st = hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, counts.data(), s);
+      r = hm::run_batch(g, patterns, modes, npat, nullptr, nullptr, counts.data(), s);
       const auto t1 = std::chrono::steady_clock::now();
-      if (st != HM_OK) break;
+      if (r != HM_OK) return r;
+      if (counts != ref) return HM_ERR_CUDA;
       t_min = std::min(t_min, std::chrono::duration<double, std::milli>(t1 - t0).count());
     }
-    if (st != HM_OK || counts != ref) {  // a knob never changes results; treat a mismatch as failure
-      hm_set_tuning(&before);
-      return st != HM_OK ? st : HM_ERR_CUDA;
+    *t_out = t_min;
+    return HM_OK;
+  };
+  hm_tuning pick{};
+  hm_get_tuning(&pick);  // the current setting, defaults filled in
+  double best_t = 0;
+  st = measure(pick, &best_t);
+  // coordinate descent: one knob at a time over its candidate values, keeping
+  // a change only when it is faster by more than 1 %; passes repeat until one
+  // changes nothing or the budget is spent
+  const std::vector<hm::Dim> dims = hm::tune_dims();
+  bool improved = true, out_of_time = false;
+  for (int pass = 0; st == HM_OK && improved && !out_of_time && pass < 4; ++pass) {
+    improved = false;
+    for (const hm::Dim &d : dims) {
+      if (st != HM_OK || out_of_time) break;
+      for (int32_t v : d.values) {
+        if (pick.*d.field == v) continue;
+        hm_tuning c = pick;
+        c.*d.field = v;
+        double t = 0;
+        st = measure(c, &t);
+        if (st != HM_OK) break;
+        if (t < best_t * 0.99) {
+          best_t = t;
+          pick = c;
+          improved = true;
+        }
+        if (budget_ms && spent_ms() > (double)budget_ms) {
+          out_of_time = true;
+          break;
+        }
+      }
     }
-    if (t_min < best_t) {
-      best_t = t_min;
-      pick = c;
-    }
-    const double spent = std::chrono::duration<double, std::milli>(
-                             std::chrono::steady_clock::now() - t_start).count();
-    if (budget_ms && spent > (double)budget_ms) break;
+  }
+  if (st != HM_OK) {
+    hm_set_tuning(&before);
+    return st;
   }
   hm_set_tuning(&pick);
   hm_get_tuning(best);  // with the defaults filled in
   if (best_ms) *best_ms = (float)best_t;
+  if (!key.empty()) hm::cache_store(cache_path, key, *best, (float)best_t);
   return HM_OK;
+}
+
+extern "C" hm_status hm_autotune(const hm_graph *g, const hm_pattern *const *patterns,
+                                 const int32_t *modes, int32_t npat, uint32_t budget_ms,
+                                 hm_tuning *best, float *best_ms, void *stream) {
+  return hm_autotune_cached(g, patterns, modes, npat, budget_ms, nullptr, best, best_ms, nullptr, stream);
 }

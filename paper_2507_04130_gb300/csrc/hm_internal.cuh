@@ -28,6 +28,7 @@ namespace hm {
 
 constexpr int kMaxK = HM_MAX_K;
 constexpr int kMaxCons = 2 * (HM_MAX_K - 1);
+constexpr int kMaxAut = 64;  // symmetry breaking is used for patterns with at most this many automorphisms
 static_assert(kMaxCons <= 64, "condition masks are 64-bit");
 constexpr int kWarp = 32;
 
@@ -105,7 +106,25 @@ struct Plan {
   int32_t ndefer;
   Cons cons[kMaxK][kMaxCons];
   Cons defer[kMaxCons];
+  // Symmetry breaking.  The matches of a pattern (Sec. II-A, Eqs. 1-3) fall
+  // into orbits of |Aut| maps f o s, s an automorphism of the labelled
+  // pattern.  The search keeps the one map per orbit that satisfies the order
+  // constraints below (f(p) > f(q) for bit q of sym_gt[p], f(p) < f(q) for
+  // bit q of sym_lt[p], q < p) and emits it with its |Aut| - 1 images: image
+  // s of original vertex v is the vertex at position aut[s][v].  naut = 1:
+  // no symmetry breaking (aut[0] maps each vertex to its own position).
+  int32_t naut;
+  uint32_t sym_gt[kMaxK];
+  uint32_t sym_lt[kMaxK];
+  int8_t aut[kMaxAut][kMaxK];
 };
+
+// A plan without symmetry breaking: every map is searched for itself.
+inline void strip_symmetry(Plan &P) {
+  if (P.naut <= 1) return;
+  P.naut = 1;  // aut[0] is the identity
+  for (int i = 0; i < kMaxK; ++i) P.sym_gt[i] = P.sym_lt[i] = 0;
+}
 
 // Budget / status words shared by all warps of one call.
 enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
@@ -305,6 +324,12 @@ hm_stats &tls_stats();
 bool timing_enabled();
 bool counters_enabled();
 hm_tuning tuning();  // current process-wide extension knobs (validated)
+// log2 of the warps per depth-2 state; 0 (automatic) gives 4 warps to shared
+// position-0 states (few, each standing for up to 32 states) and 1 otherwise.
+inline int32_t wps_shift(const hm_tuning &t, bool shared = false) {
+  if (t.warps_per_state == 0) return shared ? 2 : 0;
+  return t.warps_per_state >= 4 ? 2 : t.warps_per_state >= 2 ? 1 : 0;
+}
 uint64_t budget_ms();
 uint64_t budget_chunks();
 

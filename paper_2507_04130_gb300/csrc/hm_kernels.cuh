@@ -104,7 +104,8 @@ struct ExtArgs {
   int32_t seeds_per_fetch;  // seeds a warp claims at once
   uint32_t poll_mask;       // a busy warp looks for donation requests every poll_mask+1 chunks
   int32_t leaf_flatten;     // run the last depth of all survivors of a chunk together
-  int32_t pad3;
+  int32_t wps_shift;        // log2 of the warps per depth-2 state: each state's first
+                            // extension range is split into that many parts, one per claim
   const int2 *seeds;
   const unsigned long long *nseeds;
   Task *qbuf;
@@ -453,6 +454,42 @@ __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int 
   }
 }
 
+// Symmetry breaking (Plan::naut > 1): candidate c for position p keeps the
+// order constraints against earlier positions; position L's image is lc when
+// it is not yet in S.map (the flattened leaf), otherwise pass L = p.
+__device__ __noinline__ bool sym_ok(const Plan &P, const WarpState &S, int p, int32_t c, int L = -1,
+                                    int32_t lc = 0) {
+  uint32_t g = P.sym_gt[p], l = P.sym_lt[p];
+  while (g) {
+    const int q = __ffs(g) - 1;
+    g &= g - 1;
+    if (c <= (q == L ? lc : S.map[q])) return false;
+  }
+  while (l) {
+    const int q = __ffs(l) - 1;
+    l &= l - 1;
+    if (c >= (q == L ? lc : S.map[q])) return false;
+  }
+  return true;
+}
+
+// The rows of one found map and of its automorphic images, P.naut rows from
+// row r on: image s of original vertex v is the vertex at position
+// P.aut[s][v].  Positions below `nmapped` are in map[]; position nmapped is
+// e1 and the one after it e2.  Out of line: only symmetric patterns use it.
+__device__ __noinline__ void write_match_rows(const Plan &P, int32_t *row_base, unsigned long long r,
+                                              unsigned long long row_cap, const int32_t *map, int nmapped,
+                                              int32_t e1, int32_t e2) {
+  const int k = P.k;
+  for (int s = 0; s < P.naut && r + s < row_cap; ++s) {
+    int32_t *row = row_base + (r + s) * k;
+    for (int v = 0; v < k; ++v) {
+      const int i = P.aut[s][v];
+      row[v] = i < nmapped ? map[i] : (i == nmapped ? e1 : e2);
+    }
+  }
+}
+
 // Find the group (arc label, vertex label) in a directory span; {first, length} or {0, 0}.
 template <bool kC>
 __device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t first, int32_t cnt,
@@ -507,7 +544,7 @@ __device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, Wa
 
 // Does candidate c (taken from the driving group, so its arc label and vertex
 // label already match) satisfy every other condition of position p?
-template <bool kC>
+template <bool kC, bool kSym>
 __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P,
                                                 const WarpState &S, const int2 *__restrict__ grp,
                                                 int p, int drive, int32_t c, bool leaf,
@@ -515,6 +552,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
   for (int i = 0; i < p; ++i)
     if (S.map[i] == c) return false;                        // injective
   if (root_mask && p == P.root_pos && !root_mask[c]) return false;
+  if (kSym && (P.sym_gt[p] | P.sym_lt[p]) && !sym_ok(P, S, p, c)) return false;
   const int nc = P.ncons[p];
   // c's own degrees: needed for the degree filter (inner levels) and to search
   // c's shorter list instead of a hub's; its offsets only for such a search
@@ -581,7 +619,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
 // One condition j of position p on candidate c (the j-th entry of cons[p]).
 // The lane with `base` set also applies the per-candidate checks
 // (injectivity, root mask, degree filter on inner levels).
-template <bool kC>
+template <bool kC, bool kSym>
 __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const WarpState &S,
                                           const int2 *__restrict__ grp, int p, int j, int32_t c,
                                           bool base, bool leaf, const uint8_t *root_mask,
@@ -590,6 +628,7 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
     for (int i = 0; i < p; ++i)
       if (S.map[i] == c) return false;
     if (root_mask && p == P.root_pos && !root_mask[c]) return false;
+    if (kSym && (P.sym_gt[p] | P.sym_lt[p]) && !sym_ok(P, S, p, c)) return false;
   }
   if (kC) ctr += 16;
   const int4 vi = __ldg(&G.vi[c]);
@@ -689,7 +728,7 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
   return true;
 }
 
-template <bool kC>
+template <bool kC, bool kSym>
 __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, const WarpState &S,
                                            const int2 *__restrict__ grp, int p, int drive, int32_t d,
                                            const LeafOwner &o, const uint8_t *root_mask,
@@ -699,6 +738,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
   for (int i = 0; i < L; ++i)
     if (S.map[i] == d) return false;                        // injective
   if (root_mask && p == P.root_pos && !root_mask[d]) return false;
+  if (kSym && (P.sym_gt[p] | P.sym_lt[p]) && !sym_ok(P, S, p, d, L, o.c)) return false;
   const int nc = P.ncons[p];
   if (nc <= 1) return true;
   if (G.filt_min >= 0) {
@@ -863,7 +903,7 @@ __device__ void expand_position1(const DevGraph &G, const Plan &P, const WarpSta
 // Runs the leaf of every survivor in `m` (bits over adj[base + lane]) that has
 // at most kFlatMax leaf candidates; returns the survivors left for the
 // ordinary descent.  Adds the matches to task_count and writes their rows.
-template <bool kRows, bool kC, bool kShared>
+template <bool kRows, bool kC, bool kShared, bool kSym>
 __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S, const ExtArgs &A,
                                  int2 *__restrict__ grp, int L, const int32_t *__restrict__ adj,
                                  int32_t base, uint32_t m, int lane, const uint8_t *root_mask,
@@ -873,6 +913,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
   const int k = P.k;
   const int npos = P.npos[p];
   // label groups of anchors mapped before depth L are the same for every survivor
+  bool dead = false;
   for (int j = 0; j < npos; ++j) {
     const Cons cs = P.cons[p][j];
     if (cs.q == L) continue;
@@ -880,6 +921,14 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     const int2 r = cs.kind == kOut ? dir_lookup<kC>(G.gdir_out, dq.x, dq.y, cs.lab, P.vlab[p], lane, ctr)
                                    : dir_lookup<kC>(G.gdir_in, dq.z, dq.w, cs.lab, P.vlab[p], lane, ctr);
     if (lane == 0) grp[P.gbase[p] + j] = r;
+    dead |= r.y == 0;
+  }
+  if (dead) {
+    // an anchor mapped before L has no neighbour the leaf could take: no
+    // survivor of depth L, now or in the prefix's later chunks, can match
+    if (lane == 0) S.hi[L] = S.lo[L];
+    __syncwarp();
+    return 0;
   }
   __syncwarp();
   // each survivor lane: its record, its own label groups, its shortest range
@@ -985,27 +1034,33 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     }
     const LeafOwner &oo = S.owners[ow];
     bool ok = false;
-    if (g < total) ok = check_leaf<kC>(G, P, S, grp, p, S.owner_drive[ow].x, d, oo, root_mask, ctr);
+    if (g < total) ok = check_leaf<kC, kSym>(G, P, S, grp, p, S.owner_drive[ow].x, d, oo, root_mask, ctr);
     if (kShared) {
       expand_position1<kRows, kC>(G, P, S, A, ok, L, oo.c, d, lane, task_count, S.row_cursor, S.row_base,
                                   S.row_cap, ctr);
       continue;
     }
     const uint32_t bal = __ballot_sync(kFull, ok);
-    const int nm = __popc(bal);
+    const int nm = __popc(bal) * (kSym ? P.naut : 1);
     task_count += nm;
     if (kRows && nm) {
       unsigned long long at = 0;
       if (lane == 0) at = atomicAdd(S.row_cursor, (unsigned long long)nm);
       at = __shfl_sync(kFull, at, 0);
       if (ok) {
-        const unsigned long long r = at + __popc(bal & lanemask_lt());
-        if (r < S.row_cap) {
-          if (kC) ctr += 4 * k;
-          int32_t *row = S.row_base + r * k;
-          for (int i = 0; i < L; ++i) row[P.orig[i]] = S.map[i];
-          row[P.orig[L]] = oo.c;
-          row[P.orig[p]] = d;
+        if (!kSym || P.naut == 1) {
+          const unsigned long long r = at + __popc(bal & lanemask_lt());
+          if (r < S.row_cap) {
+            if (kC) ctr += 4 * k;
+            int32_t *row = S.row_base + r * k;
+            for (int i = 0; i < L; ++i) row[P.orig[i]] = S.map[i];
+            row[P.orig[L]] = oo.c;
+            row[P.orig[p]] = d;
+          }
+        } else {
+          if (kC) ctr += 4ull * k * P.naut;
+          write_match_rows(P, S.row_base, at + (unsigned long long)__popc(bal & lanemask_lt()) * P.naut,
+                           S.row_cap, S.map, L, oo.c, d);
         }
       }
     }
@@ -1238,7 +1293,7 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int ngrp) {
   return (sizeof(WarpState) + sizeof(int2) * (size_t)ngrp + 15) / 16 * 16;
 }
 
-template <bool kRows, bool kC, int kMinBlocks, bool kBatch, bool kShared = false>
+template <bool kRows, bool kC, int kMinBlocks, bool kBatch, bool kShared = false, bool kSym = false>
 __global__ void __launch_bounds__(kExtThreads, kMinBlocks)
 k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
          const __grid_constant__ ExtArgs A) {
@@ -1250,7 +1305,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
   int2 *grp = reinterpret_cast<int2 *>(s_raw + (threadIdx.x >> 5) * stride + sizeof(WarpState));
   if (lane == 0) {
     S.deadline = globaltimer_ns() + A.budget_ns;
-    S.nseeds = *A.nseeds;
+    S.nseeds = *A.nseeds << A.wps_shift;  // claims: (state, part) pairs
     S.seed_at = S.seed_end = 0;
     S.my_count = 0;
     S.chunks_flushed = 0;
@@ -1282,9 +1337,10 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
       }
       __syncwarp();
       if (s < seed_end) {
+        const unsigned long long si = s >> A.wps_shift;  // the depth-2 state of this claim
         if (kShared) {
           // a shared position-0 state: position 1 is chosen at the leaves
-          const int4 gr = A.groups[s];
+          const int4 gr = A.groups[si];
           if (kC && lane == 0) ctr += 16;
           set_mapped<kC>(G, S, 0, gr.x, lane, ctr);
           set_mapped<kC>(G, S, 1, -1, lane, ctr);
@@ -1293,11 +1349,19 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
             S.vhi = gr.z;
           }
         } else {
-          const int2 uv = A.seeds[s];
-          if (kBatch) pid = A.seed_pid[s];
+          const int2 uv = A.seeds[si];
+          if (kBatch) pid = A.seed_pid[si];
           if (kC && lane == 0) ctr += kBatch ? 12 : 8;
           set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
           set_mapped<kC>(G, S, 1, uv.y, lane, ctr);
+          // symmetry breaking between positions 0 and 1: the seed is kept by
+          // the extension, not by the validators, so the injected states stay
+          // exactly the validators' output
+          const Plan &Ps = kBatch ? A.plans[pid] : P0;
+          if (kSym && ((Ps.sym_gt[1] && uv.y <= uv.x) || (Ps.sym_lt[1] && uv.y >= uv.x))) {
+            __syncwarp();
+            continue;
+          }
         }
         __syncwarp();
         got = 1;
@@ -1324,9 +1388,10 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
     __syncwarp();
     unsigned long long task_count = 0;
     if (got == 1) {
+      const int part = (int)((S.seed_at - 1) & ((1ull << A.wps_shift) - 1));  // this claim's share of the state
       if (kBatch && k == 2) {
-        // a two-vertex pattern: the validated seed is the whole match
-        if (lane == 0) {
+        // a two-vertex pattern: the validated seed is the whole match (taken by part 0)
+        if (lane == 0 && part == 0) {
           atomicAdd(&A.counts[pid], 1ull);
           if (kRows) {
             const unsigned long long r = atomicAdd(S.row_cursor, 1ull);
@@ -1340,6 +1405,16 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         continue;
       }
       setup_level<kC>(G, P, S, grp, 2, lane, false, ctr);
+      if (A.wps_shift) {
+        // several warps share the state: this one takes part `part` of its
+        // depth-2 candidate range
+        __syncwarp();
+        if (lane == 0) {
+          const int64_t lo = S.lo[2], len = (int64_t)S.hi[2] - lo, w = 1ll << A.wps_shift;
+          S.lo[2] = (int32_t)(lo + len * part / w);
+          S.hi[2] = (int32_t)(lo + len * (part + 1) / w);
+        }
+      }
     }
     int L0 = 2;
     uint32_t first_mask = kFull;
@@ -1420,7 +1495,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
               ctr += 4;
               ++lanes;
             }
-            pass = check_one<kC>(G, P, S, grp, level, slot < drive ? slot : slot + 1, cc, slot == 0,
+            pass = check_one<kC, kSym>(G, P, S, grp, level, slot < drive ? slot : slot + 1, cc, slot == 0,
                                  leaf, A.root_mask, ctr);
           }
           const uint32_t bal = __ballot_sync(kFull, pass);
@@ -1441,7 +1516,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
               ctr += 4;
               ++lanes;
             }
-            ok = check_candidate<kC>(G, P, S, grp, level, drive, c, leaf, A.root_mask, ctr);
+            ok = check_candidate<kC, kSym>(G, P, S, grp, level, drive, c, leaf, A.root_mask, ctr);
           }
           m = __ballot_sync(kFull, ok);
         }
@@ -1458,21 +1533,25 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           continue;
         }
         if (leaf) {
-          // leaf: every survivor is a match
-          const int nm = __popc(m);
+          // leaf: every survivor is a match (with its automorphic images)
+          const int nm = __popc(m) * (kSym ? P.naut : 1);
           task_count += nm;
           if (kRows && nm) {
             unsigned long long at = 0;
             if (lane == 0) at = atomicAdd(S.row_cursor, (unsigned long long)nm);
             at = __shfl_sync(kFull, at, 0);
-            if (ok) {
-              unsigned long long r = at + __popc(m & lanemask_lt());
+            if (ok && (!kSym || P.naut == 1)) {
+              const unsigned long long r = at + __popc(m & lanemask_lt());
               if (r < S.row_cap) {
                 if (kC) ctr += 4 * k;
                 int32_t *row = S.row_base + r * k;
                 for (int i = 0; i < k - 1; ++i) row[P.orig[i]] = S.map[i];
                 row[P.orig[k - 1]] = c;
               }
+            } else if (ok) {
+              if (kC) ctr += 4ull * k * P.naut;
+              write_match_rows(P, S.row_base, at + (unsigned long long)__popc(m & lanemask_lt()) * P.naut,
+                               S.row_cap, S.map, k - 1, c, 0);
             }
           }
           __syncwarp();
@@ -1480,7 +1559,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         }
         uint32_t pending = m;
         if (A.leaf_flatten && level == k - 2 && m)
-          pending = leaf_flatten<kRows, kC, kShared>(G, P, S, A, grp, level, adj, lo, m, lane, A.root_mask,
+          pending = leaf_flatten<kRows, kC, kShared, kSym>(G, P, S, A, grp, level, adj, lo, m, lane, A.root_mask,
                                             task_count, A.ctl, my_chunks, ctr);
         if (lane == 0) {
           S.mask[level] = pending;
@@ -1609,43 +1688,46 @@ int min_blocks_slot(int min_blocks) {
   return 0;
 }
 
-template <bool R, bool C, bool B, bool S>
+template <bool R, bool C, bool B, bool S, bool Y>
 ExtendKernel extend_kernel_mb(int slot) {
   switch (slot) {
-    case 1: return k_extend<R, C, 5, B, S>;
-    case 2: return k_extend<R, C, 6, B, S>;
-    default: return k_extend<R, C, 4, B, S>;
+    case 1: return k_extend<R, C, 5, B, S, Y>;
+    case 2: return k_extend<R, C, 6, B, S, Y>;
+    default: return k_extend<R, C, 4, B, S, Y>;
   }
 }
 
-template <bool B, bool S>
+template <bool B, bool S, bool Y>
 ExtendKernel extend_kernel_s(bool rows, bool counters, int slot) {
   if (rows)
-    return counters ? extend_kernel_mb<true, true, B, S>(slot) : extend_kernel_mb<true, false, B, S>(slot);
-  return counters ? extend_kernel_mb<false, true, B, S>(slot) : extend_kernel_mb<false, false, B, S>(slot);
+    return counters ? extend_kernel_mb<true, true, B, S, Y>(slot) : extend_kernel_mb<true, false, B, S, Y>(slot);
+  return counters ? extend_kernel_mb<false, true, B, S, Y>(slot) : extend_kernel_mb<false, false, B, S, Y>(slot);
 }
 
 // The extension kernel for a launch; `shared` (shared position-0 states)
-// exists for single-pattern launches only.
+// exists for single-pattern launches only, and never with symmetry breaking
+// (`sym`: some pattern of the launch has a plan with naut > 1).
 template <bool B = false>
-ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0, bool shared = false) {
+ExtendKernel extend_kernel(bool rows, bool counters, int slot = 0, bool shared = false, bool sym = false) {
   if constexpr (!B) {
-    if (shared) return extend_kernel_s<false, true>(rows, counters, slot);
+    if (shared) return extend_kernel_s<false, true, false>(rows, counters, slot);
   }
-  return extend_kernel_s<B, false>(rows, counters, slot);
+  return sym ? extend_kernel_s<B, false, true>(rows, counters, slot)
+             : extend_kernel_s<B, false, false>(rows, counters, slot);
 }
 
 // Resident blocks of an extension kernel variant for a dynamic shared-memory size.
 template <bool B = false>
-int extend_grid(bool rows, bool counters, size_t smem, int slot = 0, bool shared = false) {
-  static std::atomic<int> cache[3][8][64];  // zero-initialised (static storage)
+int extend_grid(bool rows, bool counters, size_t smem, int slot = 0, bool shared = false, bool sym = false) {
+  static std::atomic<int> cache[3][16][64];  // zero-initialised (static storage)
   const int sm = (int)std::min<size_t>(smem / 1024, 63);
-  std::atomic<int> &c = cache[slot][(shared ? 4 : 0) + (rows ? 2 : 0) + (counters ? 1 : 0)][sm];
+  std::atomic<int> &c =
+      cache[slot][(sym ? 8 : 0) + (shared ? 4 : 0) + (rows ? 2 : 0) + (counters ? 1 : 0)][sm];
   int v = c.load(std::memory_order_relaxed);
   if (!v) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, extend_kernel<B>(rows, counters, slot, shared), kExtThreads, smem);
+        &per_sm, extend_kernel<B>(rows, counters, slot, shared, sym), kExtThreads, smem);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       return 0;

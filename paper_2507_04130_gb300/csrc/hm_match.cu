@@ -17,6 +17,7 @@ enum class Want { kCount, kRows, kStates };
 // become P.defer, read from the chosen image v of position 1.
 Plan shared_plan(const Plan &P) {
   Plan Q = P;
+  strip_symmetry(Q);  // position 1 is chosen at the leaves; its images are not permuted there
   Q.ndefer = 0;
   for (int p = 2; p < P.k; ++p) {
     int c = 0;
@@ -43,9 +44,12 @@ __global__ void k_seed_group_flags(const int2 *__restrict__ s, int64_t n, int64_
 
 // Seeds per shared group in induced calls: each group's (match, image) pairs
 // are checked by its own warp at the leaf, so a hub's hundreds of seeds are
-// split into groups of this size, which keeps that loop short while the
-// search over the later positions still runs once per 32 seeds instead of
-// once per seed.
+// split into groups of at most this size, which keeps that loop short while
+// the search over the later positions still runs about once per 32 seeds
+// instead of once per seed.  The cuts fall at every 32nd seed of the whole
+// sorted seed list (global alignment), not at every 32nd seed of one image,
+// so an image's first and last groups can be smaller: an image with n seeds
+// gets at most ceil(n/32) + 1 groups.
 constexpr int64_t kInducedGroupCap = 32;
 
 // One int4 {u, first, end, 0} per group; idx is the exclusive scan of flag.
@@ -88,7 +92,9 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     if (root < 0 || root >= p->k) return HM_ERR_ARG;
     for (int i = 0; i < p->k; ++i)
       if (plan.orig[i] == root) plan.root_pos = i;
+    strip_symmetry(plan);  // the root restriction is on one map, not on its orbit
   }
+  if (tuning().symmetry < 0) strip_symmetry(plan);
   const DevGraph G = g->dev();
   const int64_t m = g->m;
   Scratch sc(s);
@@ -224,13 +230,15 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.seeds_per_fetch = tu.seeds_per_fetch;
     A.poll_mask = (uint32_t)tu.poll_every - 1u;
     A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
+    A.wps_shift = wps_shift(tu, share);
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
-    const int grid = extend_grid(rows, counters, smem, slot, share);
+    const bool sym = plan.naut > 1;
+    const int grid = extend_grid(rows, counters, smem, slot, share, sym);
     if (grid <= 0) return HM_ERR_CUDA;
     st.extend_grid = grid;
     st.extend_block = kExtThreads;
-    extend_kernel(rows, counters, slot, share)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    extend_kernel(rows, counters, slot, share, sym)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
     ++launches;
     t_ext.stop();
     HM_CUDA_TRY(cudaGetLastError());
@@ -326,6 +334,9 @@ extern "C" hm_status hm_injected_states(const hm_graph *g, const hm_pattern *p, 
 
 // ---------------------------------------------------------------------------
 // Counting without any device allocation (hm_count_matches_static).
+// It runs one search per depth-2 state: grouping the states by their
+// position-0 image (share_seeds) sorts them into temporary buffers that the
+// fixed array has no room for.
 //
 // Some callers cannot allocate device memory while they match: a process
 // whose device memory is carved up in advance by another allocator (a
@@ -399,7 +410,8 @@ extern "C" hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern
 
   hm_stats &st = tls_stats();
   std::memset(&st, 0, sizeof(st));
-  const Plan &plan = p->plan[mode];
+  Plan plan = p->plan[mode];
+  if (tuning().symmetry < 0) strip_symmetry(plan);
   const DevGraph G = g->dev();
   const int64_t m = g->m;
   const int sms = num_sms();
@@ -448,11 +460,13 @@ extern "C" hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern
     A.seeds_per_fetch = tu.seeds_per_fetch;
     A.poll_mask = (uint32_t)tu.poll_every - 1u;
     A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
+    A.wps_shift = wps_shift(tu);
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
-    const int grid = extend_grid(false, false, smem, slot);
+    const bool sym = plan.naut > 1;
+    const int grid = extend_grid(false, false, smem, slot, false, sym);
     if (grid <= 0) return HM_ERR_CUDA;
-    extend_kernel(false, false, slot)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
+    extend_kernel(false, false, slot, false, sym)<<<grid, kExtThreads, smem, s>>>(G, plan, A);
     ++launches;
   }
   HM_CUDA_TRY(cudaGetLastError());

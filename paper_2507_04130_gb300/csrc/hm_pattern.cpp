@@ -23,8 +23,11 @@
 //     become "arc must exist with this label" conditions, and in induced mode
 //     the missing ones become "arc must not exist" conditions.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "hm_internal.cuh"
 
@@ -155,6 +158,111 @@ void build_plan(const PatternGraph &P, const int32_t *order, int induced, hm::Pl
   pl.ngrp = slots;
 }
 
+// ---- symmetry breaking ---------------------------------------------------------
+//
+// An automorphism of the labelled pattern is a permutation s of its vertices
+// that keeps every vertex label and maps every arc onto an arc with the same
+// label (so non-arcs onto non-arcs).  If f is a match (Eqs. 1-3, either mode),
+// so is f o s, and the |Aut| maps f o s are distinct: the matches fall into
+// orbits of exactly |Aut|.  Order constraints chosen as by Grochow and Kellis
+// (RECOMB 2007) keep exactly one map per orbit: while the group G is not
+// trivial, take a vertex v of a largest G-orbit, require f(v) < f(w) for every
+// other w in that orbit, and continue with the stabiliser of v.  (For any f
+// the images f o s, s in G, that satisfy the first constraints are those
+// sending v to the orbit member with the smallest image: a coset of the
+// stabiliser, on which the next constraints act the same way.)
+
+using Perm = std::array<int8_t, HM_MAX_K>;
+
+// Every automorphism by backtracking over the vertices in id order; false
+// when there are more than `cap`.
+bool enumerate_automorphisms(const PatternGraph &P, int cap, std::vector<Perm> &out) {
+  const int k = P.k;
+  Perm s{};
+  bool used[HM_MAX_K] = {};
+  bool over = false;
+  auto rec = [&](auto &&self, int i) -> void {
+    if (over) return;
+    if (i == k) {
+      if ((int)out.size() >= cap) {
+        over = true;
+        return;
+      }
+      out.push_back(s);
+      return;
+    }
+    for (int u = 0; u < k && !over; ++u) {
+      if (used[u] || P.vlab[u] != P.vlab[i] || P.indeg[u] != P.indeg[i] || P.outdeg[u] != P.outdeg[i])
+        continue;
+      bool ok = true;
+      for (int j = 0; j < i && ok; ++j) {
+        const int sj = s[j];
+        if (P.arc[i][j] != P.arc[u][sj] || (P.arc[i][j] && P.lab[i][j] != P.lab[u][sj])) ok = false;
+        if (P.arc[j][i] != P.arc[sj][u] || (P.arc[j][i] && P.lab[j][i] != P.lab[sj][u])) ok = false;
+      }
+      if (!ok) continue;
+      s[i] = (int8_t)u;
+      used[u] = true;
+      self(self, i + 1);
+      used[u] = false;
+    }
+  };
+  rec(rec, 0);
+  return !over;
+}
+
+// Fills the plans' symmetry fields for the search order `order` (position ->
+// original vertex); leaves naut = 1 (no symmetry breaking) for two-vertex
+// patterns and for patterns with more than kMaxAut automorphisms.
+void add_symmetry(const PatternGraph &P, const int32_t *order, hm::Plan *plans, int nplans) {
+  const int k = P.k;
+  int pos[HM_MAX_K];
+  for (int i = 0; i < k; ++i) pos[order[i]] = i;
+  for (int m = 0; m < nplans; ++m) {
+    hm::Plan &pl = plans[m];
+    pl.naut = 1;
+    for (int v = 0; v < k; ++v) pl.aut[0][v] = (int8_t)pos[v];
+    for (int p = 0; p < k; ++p) pl.sym_gt[p] = pl.sym_lt[p] = 0;
+  }
+  if (k < 3) return;
+  std::vector<Perm> group;
+  if (!enumerate_automorphisms(P, hm::kMaxAut, group) || group.size() <= 1) return;
+  // constraints f(v) < f(w), as pairs of original vertices
+  std::vector<std::pair<int, int>> lt;
+  std::vector<Perm> G = group;
+  while (G.size() > 1) {
+    int best = -1, best_size = 0;
+    bool in_orbit[HM_MAX_K][HM_MAX_K] = {};
+    int orbit_size[HM_MAX_K] = {};
+    for (int v = 0; v < k; ++v) {
+      for (const Perm &g : G) in_orbit[v][g[v]] = true;
+      for (int w = 0; w < k; ++w) orbit_size[v] += in_orbit[v][w];
+    }
+    for (int v = 0; v < k; ++v)  // a largest orbit; among its vertices, the earliest in the search order
+      if (orbit_size[v] > best_size || (orbit_size[v] == best_size && best >= 0 && pos[v] < pos[best])) {
+        best = v;
+        best_size = orbit_size[v];
+      }
+    for (int w = 0; w < k; ++w)
+      if (w != best && in_orbit[best][w]) lt.emplace_back(best, w);
+    std::vector<Perm> stab;
+    for (const Perm &g : G)
+      if (g[best] == best) stab.push_back(g);
+    G.swap(stab);
+  }
+  for (int m = 0; m < nplans; ++m) {
+    hm::Plan &pl = plans[m];
+    pl.naut = (int32_t)group.size();
+    for (size_t si = 0; si < group.size(); ++si)
+      for (int v = 0; v < k; ++v) pl.aut[si][v] = (int8_t)pos[group[si][v]];
+    for (const auto &c : lt) {
+      const int pv = pos[c.first], pw = pos[c.second];  // f(v) < f(w)
+      if (pv < pw) pl.sym_gt[pw] |= 1u << pv;  // checked when w is mapped: f(w) > f(v)
+      else pl.sym_lt[pv] |= 1u << pw;          // checked when v is mapped: f(v) < f(w)
+    }
+  }
+}
+
 bool weakly_connected(const PatternGraph &P) {
   int parent[HM_MAX_K];
   for (int i = 0; i < P.k; ++i) parent[i] = i;
@@ -200,6 +308,7 @@ extern "C" hm_status hm_load_pattern(int32_t k, int32_t mp, const int32_t *src,
   structural_reorder(P, p->order);
   build_plan(P, p->order, 0, p->plan[0]);
   build_plan(P, p->order, 1, p->plan[1]);
+  add_symmetry(P, p->order, p->plan, 2);
   *out = p;
   return HM_OK;
 }
@@ -242,11 +351,18 @@ extern "C" hm_status hm_load_pattern_ordered(int32_t k, int32_t mp, const int32_
   for (int i = 0; i < k; ++i) p->order[i] = order[i];
   build_plan(P, p->order, 0, p->plan[0]);
   build_plan(P, p->order, 1, p->plan[1]);
+  add_symmetry(P, p->order, p->plan, 2);
   *out = p;
   return HM_OK;
 }
 
 extern "C" void hm_free_pattern(hm_pattern *p) { delete p; }
+
+extern "C" hm_status hm_pattern_automorphisms(const hm_pattern *p, int32_t *count) {
+  if (!p || !count) return HM_ERR_ARG;
+  *count = p->plan[0].naut;
+  return HM_OK;
+}
 
 extern "C" hm_status hm_pattern_order(const hm_pattern *p, int32_t *order_out) {
   if (!p || !order_out) return HM_ERR_ARG;

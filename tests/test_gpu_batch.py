@@ -115,8 +115,31 @@ def test_autotune_picks_valid_knobs_and_keeps_results(hm):
     ref = hm.count_batch(G, P, hm.INDUCED)
     try:
         best = hm.autotune(G, P, hm.INDUCED, budget_ms=3000)
-        assert best["extend_min_blocks"] in (4, 5, 6) and best["ms"] > 0
-        assert hm.get_tuning() == {k: v for k, v in best.items() if k != "ms"}
+        assert best["extend_min_blocks"] in (4, 5, 6) and best["ms"] > 0 and not best["from_cache"]
+        assert best["warps_per_state"] in (0, 1, 2, 4) and 1 <= best["seeds_per_fetch"] <= 64
+        assert hm.get_tuning() == {k: v for k, v in best.items() if k not in ("ms", "from_cache")}
         assert hm.count_batch(G, P, hm.INDUCED) == ref
+    finally:
+        hm.set_tuning()
+
+
+def test_autotune_cache_reuses_the_choice_per_graph_and_mix(hm, tmp_path):
+    g = synth.config2_graph(scale=11)
+    G = hm.Graph.from_synth(g)
+    pats = synth.config4_patterns(count=16)
+    P = [hm.Pattern.from_synth(p) for p in pats]
+    cache = str(tmp_path / "tune.txt")
+    try:
+        first = hm.autotune(G, P, hm.INDUCED, budget_ms=1500, cache=cache)
+        assert not first["from_cache"]
+        hm.set_tuning()
+        again = hm.autotune(G, P, hm.INDUCED, budget_ms=1500, cache=cache)
+        assert again["from_cache"]
+        strip = lambda d: {k: v for k, v in d.items() if k not in ("ms", "from_cache")}
+        assert strip(again) == strip(first) == hm.get_tuning()
+        # another pattern mix is another key: tuned afresh and appended
+        other = hm.autotune(G, P[:8], hm.INDUCED, budget_ms=800, cache=cache)
+        assert not other["from_cache"]
+        assert len(open(cache).read().splitlines()) == 2
     finally:
         hm.set_tuning()

@@ -155,6 +155,19 @@ def test_injected_states_equal_plain_validators(hm, seed):
             np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("case", _golden.match_cases("states_by_hand.txt"), ids=lambda c: c.name)
+def test_injected_states_hand_worked(hm, case):
+    """The hand-worked states in which the position-1 degree threshold or the
+    neighbour-overlap threshold alone rejects an arc (Alg. 3, reading R8)."""
+    G = hm.Graph.from_synth(case.graph())
+    P = hm.Pattern.from_synth(case.pattern())
+    for mode_name, (_, states) in case.expect.items():
+        mode = oracle.MONO if mode_name == "mono" else oracle.INDUCED
+        got = hm.injected_states(G, P, mode).cpu().numpy().reshape(-1, 2)
+        got = got[np.lexsort((got[:, 1], got[:, 0]))]
+        np.testing.assert_array_equal(got, np.array(states, np.int32).reshape(-1, 2))
+
+
 # ---------------------------------------------------------------------------
 # full matching, small and medium inputs
 # ---------------------------------------------------------------------------
@@ -392,7 +405,10 @@ def test_instrumented_kernels_agree_and_count_bytes(hm):
                                    dict(leaf_flatten=-1, pair_mode=1, split_min=2),
                                    dict(split_min=1000, seeds_per_fetch=64),
                                    dict(arc_filter=-1), dict(arc_filter=1),
-                                   dict(arc_filter=1, leaf_flatten=-1, pair_mode=1)])
+                                   dict(arc_filter=1, leaf_flatten=-1, pair_mode=1),
+                                   dict(warps_per_state=2), dict(warps_per_state=4, seeds_per_fetch=3),
+                                   dict(warps_per_state=4, leaf_flatten=-1, split_min=2),
+                                   dict(warps_per_state=2, symmetry=-1, arc_filter=-1)])
 def test_tuning_knobs_never_change_results(hm, knobs):
     g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
     g = synth.Graph(g0.n, g0.src, g0.dst, (g0.vlab % 2).astype(np.int32), g0.elab % 2)
@@ -479,7 +495,8 @@ def test_shared_position0_states_equal_the_oracle(hm, seed):
 
 
 @pytest.mark.parametrize("knobs", [dict(arc_filter=-1), dict(leaf_flatten=-1), dict(pair_mode=1, split_min=2),
-                                   dict(split_min=2, poll_every=1)])
+                                   dict(split_min=2, poll_every=1), dict(warps_per_state=4),
+                                   dict(warps_per_state=2, seeds_per_fetch=5)])
 def test_shared_position0_states_with_other_knobs(hm, knobs):
     g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
     g = synth.Graph(g0.n, g0.src, g0.dst, (g0.vlab % 2).astype(np.int32), g0.elab % 2)
