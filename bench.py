@@ -55,8 +55,18 @@ def parse_args(argv=None):
                     help="instead: every workload (ER, R-MAT, connectome, batched, served) with mean and 95%% CI "
                          "of repeated runs, per-kernel rates and the oracle on 1 and on all host cores")
     ap.add_argument("--repeats", type=int, default=7, help="runs per figure in --report")
+    ap.add_argument("--profile", choices=["rmat", "connectome"],
+                    help="instead: a short run for profilers -- load one workload and run each of its "
+                         "queries --steps times (rmat: the induced motifs with rows; connectome: the five "
+                         "5-vertex patterns, count only), no timing, no extras")
+    ap.add_argument("--conn-arcs", type=int, default=142_500_000,
+                    help="distinct arcs drawn for the connectome-shaped graph before the 5%% reciprocal "
+                         "ones are added (--profile connectome; default = the full workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="arrival window per rate of the served workload on the primary (connectome-shaped) "
+                         "graph, at most 2,000 queries per rate; a third of it on the R-MAT graph")
     return ap.parse_args(argv)
 
 
@@ -178,18 +188,18 @@ class ClockSampler:
 # CPU oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(g, pats, mode, target_s, seed=0, og=None):
+def oracle_sample(g, pats, mode, target_s, seed=0, og=None, threads=None):
     """Time the oracle on the workload restricted to a seeded random subset of root vertices.
 
-    Returns (matches, seconds, roots, threads).  The root set is grown until the
-    sample costs about `target_s` seconds of wall time.
+    Returns (matches, seconds, roots, threads, oracle graph).  The root set is
+    grown until the sample costs about `target_s` seconds of wall time.
     """
     import numpy as np
 
     import oracle
 
     og = og or oracle.OracleGraph.from_synth(g)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     rng = np.random.default_rng(seed)
     perm = rng.permutation(g.n)
     roots = 1024
@@ -272,6 +282,7 @@ def run_gpu(args):
     clocks = ClockSampler(local).start()
     time.sleep(0.3)   # let the sampler start before the timed region
     events, ext_ms, edge_ms, sort_ms = [], [[] for _ in P], [[] for _ in P], [[] for _ in P]
+    ovl_ms = [[] for _ in P]
     launches, matches = 0, 0
     torch.cuda.synchronize()
     barrier()
@@ -288,6 +299,7 @@ def run_gpu(args):
             ext_ms[i].append(st["ms_extend"])
             edge_ms[i].append(st["ms_edge_scan"])
             sort_ms[i].append(st["ms_sort"])
+            ovl_ms[i].append(st["ms_overlap"])
             matches += int(rows.shape[0])
             events.append((s, i, e0, e1))
         if dist is not None:
@@ -306,21 +318,38 @@ def run_gpu(args):
 
     # algorithmic bytes of each kernel: one instrumented pass (not timed)
     hm.set_counters(True)
-    bytes_ext, bytes_edge = [], []
+    bytes_ext, bytes_edge, bytes_ovl, states = [], [], [], []
     for i in range(len(P)):
         query(i)
         st = hm.last_stats()
         bytes_ext.append(int(st["bytes_extend"]))
         bytes_edge.append(int(st["bytes_edge_scan"]))
+        bytes_ovl.append(int(st["bytes_overlap"]))
+        states.append(int(st["states_injected"]))
     hm.set_counters(False)
 
     peak, peak_src = hbm_peak()
     mean_ext = [statistics.mean(x) for x in ext_ms]
     mean_edge = [statistics.mean(x) for x in edge_ms]
+    mean_ovl = [statistics.mean(x) for x in ovl_ms]
+    mean_sort = [statistics.mean(x) for x in sort_ms]
     achieved_ext = sum(bytes_ext) / (sum(mean_ext) / 1e3) / 1e9
     achieved_edge = sum(bytes_edge) / (sum(mean_edge) / 1e3) / 1e9
     workload_key = f"rmat{args.scale}"
     traffic = committed_traffic("k_extend", workload_key)
+    kbits = max(1, (g.n - 1).bit_length())
+    # the row sort: a stable LSD radix sort of the k-word rows, 10 key bits per
+    # pass; its inherent traffic is one read and one write of the rows per pass
+    sort_bytes = [-(-sp.k * kbits // 10) * 2 * counts[i] * sp.k * 4 for i, sp in enumerate(spats)]
+    # seed grouping of shared position-0 states (ffl_out): the seed pairs'
+    # radix sort (2 x kbits key bits) plus one pass over the flag, scan and
+    # group arrays (about 40 bytes per seed); 0 for queries that do not group
+    grp_bytes = [(-(-2 * kbits // 10) * 2 * 8 + 40) * states[i] if mean_ovl[i] > 0 and bytes_ovl[i] == 0 else 0
+                 for i in range(len(P))]
+
+    def frac_of(b, ms):
+        return round(b / (ms / 1e3) / 1e9 / peak, 4) if ms > 0 else None
+
     roofline = {
         "bound": "hbm", "kernel": "k_extend", "achieved": round(achieved_ext, 2), "peak": peak,
         "unit": "GB/s", "frac": round(achieved_ext / peak, 4),
@@ -328,15 +357,32 @@ def run_gpu(args):
         "algorithmic_bytes_per_launch": [int(b) for b in bytes_ext],
         "mean_launch_ms": [round(x, 4) for x in mean_ext],
         "kernels": {
-            "k_extend": {"ms_per_step": round(sum(mean_ext), 4), "GBps": round(achieved_ext, 2)},
+            "k_extend": {"ms_per_step": round(sum(mean_ext), 4), "GBps": round(achieved_ext, 2),
+                         "frac": round(achieved_ext / peak, 4),
+                         "bytes": "requested by the kernel (instrumented launch)"},
             "k_edge_seed": {"ms_per_step": round(sum(mean_edge), 4), "GBps": round(achieved_edge, 2),
                             "frac": round(achieved_edge / peak, 4),
-                            "algorithmic_bytes_per_launch": bytes_edge},
-            "row_sort": {"ms_per_step": round(sum(statistics.mean(x) for x in sort_ms), 4)},
+                            "algorithmic_bytes_per_launch": bytes_edge,
+                            "floor_bytes_per_launch": 12 * g.m,
+                            "floor_frac": frac_of(12 * g.m * len(P), sum(mean_edge)),
+                            "floor": "12 B per scanned arc (src, dst, label streamed once)"},
+            "k_seed_overlap_and_seed_grouping": {
+                "ms_per_step": round(sum(mean_ovl), 4),
+                "per_query_ms": [round(x, 4) for x in mean_ovl],
+                "algorithmic_bytes_per_launch": [int(a + b) for a, b in zip(bytes_ovl, grp_bytes)],
+                "frac": frac_of(sum(bytes_ovl) + sum(grp_bytes), sum(mean_ovl)),
+                "bytes": "overlap test: counted by the instrumented launch; grouping: seed-pair radix sort "
+                         "traffic + one pass over its flag/scan/group arrays"},
+            "row_sort": {"ms_per_step": round(sum(mean_sort), 4),
+                         "algorithmic_bytes_per_step": int(sum(sort_bytes)),
+                         "frac": frac_of(sum(sort_bytes), sum(mean_sort)),
+                         "bytes": "one read + one write of the rows per 10-bit LSD pass"},
         },
     }
 
-    # end to end through the public API: host pattern arrays in, host rows out
+    # end to end through the public API as a fresh caller makes it: host
+    # pattern arrays in, the count that sizes the row buffer, the rows, and
+    # the rows copied to pinned host memory
     pinned = [torch.empty(max(c, 1) * p.k, dtype=torch.int32, pin_memory=True) for c, p in zip(counts, P)]
     bi = bo = 0
     e2e_matches = 0
@@ -350,30 +396,48 @@ def run_gpu(args):
             arrays = [np.asarray(a, np.int32) for a in (sp.src, sp.dst, sp.vlab, sp.elab)]
             bi += sum(a.nbytes for a in arrays)
             Pq = hm.Pattern(sp.k, *arrays)
-            rows = hm.enumerate_matches_part(G, Pq, mode, rank, world, bufs[i])
+            c = hm.count_matches_part(G, Pq, mode, rank, world)
+            buf = torch.empty(max(c, 1) * sp.k, dtype=torch.int32, device="cuda")
+            rows = hm.enumerate_matches_part(G, Pq, mode, rank, world, buf)
             n = rows.numel()
             pinned[i][:n].copy_(rows.view(-1), non_blocking=True)
-            bo += n * 4 + 8
+            bo += n * 4 + 16
             e2e_matches += rows.shape[0]
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
     e2e_s, e2e_matches = reduce_over_ranks(e2e_s, e2e_matches, dist, "cuda")
     e2e = {"value": round(e2e_matches / e2e_s, 1), "unit": "matches/s",
            "h2d_bytes_per_step": bi // args.steps, "d2h_bytes_per_step": bo // args.steps,
-           "path": "hm.Pattern from host arrays + hm_enumerate_matches_part + D2H to pinned host"}
+           "path": ("hm.Pattern from host arrays; hm_count_matches_part to size the row buffer; "
+                    "hm_enumerate_matches_part; D2H to pinned host (wall clock)")}
 
-    batched = served = None
+    extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
-        batched = measure_batched(hm, G, torch)
-        served = measure_serving(hm, G)
+        extras["batched"] = measure_batched(hm, G, torch)
+        serving = {"secondary_rmat": measure_serving(hm, G, seconds=args.serve_seconds / 3,
+                                                     n_vlab=8, n_elab=4)}
+        extras["er_workload"] = measure_er(hm, torch)
+        conn, Gc = measure_connectome(hm, torch, flush, peak)
+        extras["connectome_workload"] = conn
+        hm.set_budget(10_000, 0)   # a served batch that needs more than 10 s is answered with HM_ERR_BUDGET
+        serving["primary_connectome"] = measure_serving(hm, Gc, seconds=args.serve_seconds, n_vlab=6, n_elab=3)
+        hm.set_budget(120_000, 0)
+        Gc.close()
+        extras["serving"] = serving
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        m_cpu, t_cpu, roots, threads, _ = oracle_sample(g, spats, 1, args.cpu_seconds)
+        m_cpu, t_cpu, roots, threads, og = oracle_sample(g, spats, 1, args.cpu_seconds)
+        m1, t1, roots1, _, _ = oracle_sample(g, spats, 1, max(2.0, args.cpu_seconds / 2), seed=1, og=og,
+                                             threads=1)
+        og.close()
         cpu = {"value": round(m_cpu / t_cpu, 1), "unit": "matches/s", "cores": threads,
                "kind": "oracle",
                "sample": (f"the 3 induced queries restricted to {roots:,} seeded random roots "
-                          f"(image of pattern vertex 0) of {g.n:,}; {m_cpu:,} matches in {t_cpu:.2f} s")}
+                          f"(image of pattern vertex 0) of {g.n:,}; {m_cpu:,} matches in {t_cpu:.2f} s"),
+               "one_thread": {"value": round(m1 / t1, 1), "unit": "matches/s", "cores": 1,
+                              "sample": (f"the same queries restricted to {roots1:,} other seeded roots; "
+                                         f"{m1:,} matches in {t1:.2f} s")}}
 
     if rank == 0:
         lat = sorted(q_ms)
@@ -396,7 +460,7 @@ def run_gpu(args):
             "step_ms": [round(x, 3) for x in step_ms],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clock,
-            "batched": batched, "serving": served,
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -449,59 +513,157 @@ def measure_batched(hm, G, torch, reps=3):
     }
 
 
-def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=3.0, max_queries=200,
-                    slots=4, max_batch=32, n_vlab=8, n_elab=4):
-    """Open-loop Poisson arrivals of motif queries against the resident graph, through hm_server."""
+def _serve(hm, G, arrivals, slots, max_batch):
+    """Replay timed arrivals against a fresh server; latency from submit to result, on the host clock."""
     import threading
 
+    n = len(arrivals)
+    srv = hm.Server(G, slots=slots, max_batch=max_batch)
+    ids = [None] * n
+    t0 = time.perf_counter()
+
+    def producer():
+        for i, (t, p, mode) in enumerate(arrivals):
+            delay = t - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(p, mode, want_rows=True)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    lat, matches, failed = [], 0, 0
+    for i in range(n):
+        while ids[i] is None:
+            time.sleep(0.0002)
+        try:
+            r = srv.result(ids[i])
+        except hm.HMError:   # e.g. the work budget ran out for this query's batch
+            failed += 1
+            continue
+        lat.append(r["latency_ms"])
+        matches += r["count"]
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat.sort()
+    nl = max(len(lat), 1)
+    return {
+        "queries": n, "failed": failed,
+        "p50_ms": round(statistics.median(lat), 3) if lat else None,
+        "p99_ms": round(lat[min(nl - 1, int(round(0.99 * (nl - 1))))], 3) if lat else None,
+        "matches": int(matches), "matches_per_s": round(matches / wall, 1),
+        "achieved_qps": round(n / wall, 1), "wall_s": round(wall, 2), "batches": st["batches"],
+        "max_inflight_batches": st["max_inflight_batches"], "rows_dropped": st["rows_dropped"],
+    }
+
+
+def measure_serving(hm, G, rates=(10, 30, 100, 300, 1000), seconds=20.0, max_queries=2000,
+                    slots=4, max_batch=32, n_vlab=8, n_elab=4, one_at_a_time=(100, 1000)):
+    """Open-loop Poisson arrivals of motif queries against the resident graph, through hm_server.
+
+    Per rate: the arrivals of `seconds` (at most max_queries) served with
+    continuous batching (`slots` dispatcher slots, batches of up to max_batch),
+    and, for the rates in one_at_a_time, the same arrivals served one query at
+    a time (one slot, batches of one) for comparison.
+    """
     import synth
 
     out = []
     for rate in rates:
         n = int(min(max_queries, max(20, rate * seconds)))
         arrivals = synth.config5_arrivals(rate, n, n_vlab=n_vlab, n_elab=n_elab)
-        srv = hm.Server(G, slots=slots, max_batch=max_batch)
-        ids = [None] * n
-        t0 = time.perf_counter()
-
-        def producer():
-            for i, (t, p, mode) in enumerate(arrivals):
-                delay = t - (time.perf_counter() - t0)
-                if delay > 0:
-                    time.sleep(delay)
-                ids[i] = srv.submit(p, mode, want_rows=True)
-
-        th = threading.Thread(target=producer)
-        th.start()
-        lat, matches, failed = [], 0, 0
-        for i in range(n):
-            while ids[i] is None:
-                time.sleep(0.0002)
-            try:
-                r = srv.result(ids[i])
-            except hm.HMError:   # e.g. the work budget ran out for this query's batch
-                failed += 1
-                continue
-            lat.append(r["latency_ms"])
-            matches += r["count"]
-        th.join()
-        wall = time.perf_counter() - t0
-        st = srv.stats()
-        srv.close()
-        lat.sort()
-        nl = max(len(lat), 1)
-        out.append({
-            "rate_qps": rate, "queries": n, "failed": failed,
-            "p50_ms": round(statistics.median(lat), 3) if lat else None,
-            "p99_ms": round(lat[min(nl - 1, int(round(0.99 * (nl - 1))))], 3) if lat else None,
-            "matches": int(matches), "matches_per_s": round(matches / wall, 1),
-            "achieved_qps": round(n / wall, 1), "batches": st["batches"],
-            "max_inflight_batches": st["max_inflight_batches"], "rows_dropped": st["rows_dropped"],
-        })
+        row = {"rate_qps": rate, "served": _serve(hm, G, arrivals, slots, max_batch)}
+        if rate in one_at_a_time:
+            row["one_at_a_time"] = _serve(hm, G, arrivals, 1, 1)
+        out.append(row)
     return {"workload": ("Poisson arrivals, k ~ U{3..7}, density U[0.4,1.0], labels uniform over the "
-                         f"graph's label sets ({n_vlab} vertex, {n_elab} arc), mode Bernoulli(1/2), rows returned, "
-                         f"resident graph; {slots} dispatcher slots, batches of up to {max_batch}"),
+                         f"graph's label sets ({n_vlab} vertex, {n_elab} arc), mode Bernoulli(1/2), rows "
+                         f"returned, resident graph; served: {slots} dispatcher slots, batches of up to "
+                         f"{max_batch}; one_at_a_time: 1 slot, batches of 1; arrival window {seconds:g} s "
+                         f"per rate, at most {max_queries} queries"),
             "rates": out}
+
+
+def measure_er(hm, torch, reps=50):
+    """The ER workload (n=1,000, m=5,000): labelled directed 3-cycle, monomorphism, count + rows,
+    and the unlabelled count; per-call latency with CUDA events."""
+    import numpy as np
+
+    import synth
+
+    g = synth.config1_graph()
+    sp = synth.config1_pattern()
+    gu = synth.Graph(g.n, g.src, g.dst, np.zeros(g.n, np.int32), np.zeros(g.m, np.int32))
+    spu = synth.Pattern(3, sp.src, sp.dst, np.zeros(3, np.int32), np.zeros(3, np.int32), "cycle3u")
+    out = {"graph": f"ER G(n={g.n}, m={g.m}), seed 0, vertex labels U{{0..3}}, arc labels U{{0..2}}",
+           "pattern": "directed 3-cycle, vertex labels (0,1,2), arc labels 0, monomorphism, count + rows"}
+    stream = torch.cuda.current_stream()
+    for key, gg, pp in (("labelled", g, sp), ("unlabelled", gu, spu)):
+        G = hm.Graph.from_synth(gg)
+        P = hm.Pattern.from_synth(pp)
+        lat, c = [], 0
+        for r in range(reps + 3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c = hm.count_matches(G, P, hm.MONO)
+            rows = hm.enumerate_matches(G, P, hm.MONO, capacity=max(c, 1))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= 3:
+                lat.append(e0.elapsed_time(e1))
+        assert rows.shape[0] == c
+        lat.sort()
+        out[key] = {"matches": int(c), "latency_ms": {"p50": round(statistics.median(lat), 4),
+                                                      "p99": round(lat[int(round(0.99 * (len(lat) - 1)))], 4),
+                                                      "calls": len(lat), "call": "count + enumerate"}}
+        G.close()
+    return out
+
+
+def measure_connectome(hm, torch, flush, peak, reps=5):
+    """The connectome-shaped workload: five 5-vertex monomorphism patterns, count only.
+
+    Returns the figures and the loaded graph (kept for the served workload).
+    """
+    import synth
+
+    t0 = time.perf_counter()
+    g = synth.cached("conn", synth.config3_graph)
+    t_gen = time.perf_counter() - t0
+    G = hm.Graph.from_synth(g)
+    hm.set_timing(True)
+    q = {}
+    for sp in synth.config3_patterns():
+        P = hm.Pattern.from_synth(sp)
+        hm.count_matches(G, P, hm.MONO)
+        tot, edge, ext, c = [], [], [], 0
+        for _ in range(reps):
+            flush.fill_(3)
+            torch.cuda.synchronize()
+            c = hm.count_matches(G, P, hm.MONO)
+            st = hm.last_stats()
+            tot.append(st["ms_edge_scan"] + st["ms_overlap"] + st["ms_extend"])
+            edge.append(st["ms_edge_scan"])
+            ext.append(st["ms_extend"])
+        hm.set_counters(True)
+        hm.count_matches(G, P, hm.MONO)
+        st = hm.last_stats()
+        hm.set_counters(False)
+        e = statistics.median(edge)
+        q[sp.name] = {"matches": int(c), "ms": round(statistics.median(tot), 3),
+                      "ms_edge_scan": round(e, 3), "ms_extend": round(statistics.median(ext), 3),
+                      "edge_scan_GBps": round(st["bytes_edge_scan"] / (e / 1e3) / 1e9, 1) if e else None,
+                      "edge_scan_frac": round(st["bytes_edge_scan"] / (e / 1e3) / 1e9 / peak, 4) if e else None,
+                      "edge_scan_floor_frac": round(12 * g.m / (e / 1e3) / 1e9 / peak, 4) if e else None,
+                      "states": int(st["states_injected"])}
+    hm.set_timing(False)
+    return {"graph": (f"connectome-shaped directed Chung-Lu, n={g.n:,}, m={g.m:,} (power-law 2.1 degrees, "
+                      "10% reciprocal), 6 vertex / 3 arc labels, seed 3"),
+            "patterns": "five random 5-vertex patterns, density U[0.5,0.8], monomorphism, count only",
+            "median_of": reps, "generate_s": round(t_gen, 1), "queries": q,
+            "edge_scan_floor": "12 B per scanned arc (src, dst, label streamed once)"}, G
 
 
 # ---------------------------------------------------------------------------
@@ -797,9 +959,40 @@ def run_report(args):
     print(json.dumps(out), flush=True)
 
 
+def run_profile(args):
+    """A minimal run for profilers: one workload, each query --steps times."""
+    import torch
+
+    import synth
+    import paper_2507_04130_gb300 as hm
+
+    torch.cuda.set_device(0)
+    if args.profile == "rmat":
+        g = synth.cached("rmat", synth.config2_graph, scale=args.scale)
+        pats, mode, rows = synth.config2_patterns(), hm.INDUCED, True
+    else:
+        n = max(1000, int(300_000 * args.conn_arcs / 142_500_000))
+        g = synth.cached("conn", synth.config3_graph, n=n, n_unique=args.conn_arcs,
+                         n_recip=args.conn_arcs // 19)
+        pats, mode, rows = synth.config3_patterns(), hm.MONO, False
+    G = hm.Graph.from_synth(g)
+    P = [hm.Pattern.from_synth(p) for p in pats]
+    counts = [hm.count_matches(G, p, mode) for p in P] if rows else None
+    for _ in range(max(1, args.steps)):
+        for i, p in enumerate(P):
+            if rows:
+                hm.enumerate_matches(G, p, mode, capacity=max(counts[i], 1))
+            else:
+                hm.count_matches(G, p, mode)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "n": g.n, "m": g.m, "queries": len(P), "steps": args.steps}))
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.report:
+    if args.profile:
+        run_profile(args)
+    elif args.report:
         run_report(args)
     elif args.ablation:
         run_ablation(args)
