@@ -268,17 +268,23 @@ hm_status hm_enumerate_batch(const hm_graph *g, const hm_pattern *const *pattern
  *
  * hm_server_create -- starts `nslots` dispatcher slots (host threads, each
  * with its own CUDA stream) serving queries against g, which must outlive the
- * server.  A free slot takes every waiting query that the device-memory
- * budget admits, up to max_batch, and runs them as one batch
- * (hm_count_batch, then hm_enumerate_batch for the queries that want rows);
+ * server.  A free slot takes the waiting queries, in arrival order, that the
+ * device-memory budget admits, up to max_batch, and runs them as one batch;
  * queries that arrive meanwhile join the next free slot's batch, and batches
- * of different slots overlap on the GPU.  Admission: each query reserves
- * 24 B x m (its worst-case seed queues) + 8 MiB while it runs; rows are
- * reserved from the count before enumeration, and a query whose rows do not
- * fit the remaining budget gets its count only (rows_dropped = 1).
- *   mem_budget  device bytes for admitted queries (0 = twice what max_batch
- *               queries per slot reserve, the second half for their rows);
- *               HM_ERR_ARG if it cannot admit one query.
+ * of different slots overlap on the GPU.  Admission by what a query needs:
+ * its seed queues, 24 B per target arc whose labels fit its seeding arc
+ * (counted per (source label, arc label, target label) when the server is
+ * created), plus 12 MiB per batch for the donation queue and control block;
+ * the search stacks live in shared memory.  The head query always runs when
+ * nothing else does, even if it alone exceeds the budget.  A batch makes one
+ * pass: the rows of each query that wants them go to a region of up to 2^18
+ * rows (fewer when the budget is short) and the batched enumeration keeps
+ * the sorted rows of every query whose count fits; only a query whose count
+ * exceeds its region runs again, at its exact size if the remaining budget
+ * holds it, else it gets its count only (rows_dropped = 1).
+ *   mem_budget  device bytes for admitted queries and their rows (0 = a
+ *               quarter of the device memory free at creation, at most
+ *               32 GiB); HM_ERR_ARG if it cannot admit one batch.
  * hm_server_submit -- validates and reorders the pattern (as hm_load_pattern,
  *   HOST arrays), queues it and returns its id at once.  mode HM_MONO or
  *   HM_INDUCED; want_rows 0/1.  Thread-safe.
@@ -418,6 +424,13 @@ hm_status hm_set_budget(uint64_t max_ms, uint64_t max_chunks);
  *                      of waiting for donations.  0 (default): automatic --
  *                      4 for shared position-0 states (share_seeds), 1
  *                      otherwise.
+ *   lookahead          1: at every inner depth before the last two, a
+ *                      candidate must have, for each class (direction, arc
+ *                      label, neighbour label) of the pattern arcs from its
+ *                      position to later ones, at least as many neighbours
+ *                      as those later positions (a labelled form of VF2's
+ *                      terminal-set look-ahead; sound, so results are
+ *                      unchanged); -1 (default): off.
  * A zero field takes its default.  HM_ERR_ARG for any other value.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -431,6 +444,7 @@ typedef struct {
   int32_t share_seeds;
   int32_t symmetry;
   int32_t warps_per_state;
+  int32_t lookahead;
 } hm_tuning;
 
 hm_status hm_set_tuning(const hm_tuning *t);

@@ -448,11 +448,12 @@ def set_counters(enabled: bool):
 
 def set_tuning(extend_min_blocks: int = 0, split_min: int = 0, pair_mode: int = 0,
                seeds_per_fetch: int = 0, poll_every: int = 0, leaf_flatten: int = 0,
-               arc_filter: int = 0, share_seeds: int = 0, symmetry: int = 0, warps_per_state: int = 0):
+               arc_filter: int = 0, share_seeds: int = 0, symmetry: int = 0, warps_per_state: int = 0,
+               lookahead: int = 0):
     """Set the extension kernel's launch knobs (0 = default; results never change)."""
     t = binding.hm_tuning(int(extend_min_blocks), int(split_min), int(pair_mode),
                           int(seeds_per_fetch), int(poll_every), int(leaf_flatten), int(arc_filter),
-                          int(share_seeds), int(symmetry), int(warps_per_state))
+                          int(share_seeds), int(symmetry), int(warps_per_state), int(lookahead))
     check(lib.hm_set_tuning(ctypes.byref(t)), "hm_set_tuning")
 
 

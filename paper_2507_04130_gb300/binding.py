@@ -76,6 +76,7 @@ class hm_tuning(ctypes.Structure):
         ("share_seeds", ctypes.c_int32),
         ("symmetry", ctypes.c_int32),
         ("warps_per_state", ctypes.c_int32),
+        ("lookahead", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -17,6 +17,7 @@ std::atomic<int> g_arc_filter{kDefaultFilterMin};
 std::atomic<int> g_share_seeds{1};
 std::atomic<int> g_symmetry{1};
 std::atomic<int> g_warps_per_state{0};  // 0: automatic
+std::atomic<int> g_lookahead{-1};
 }  // namespace
 
 hm_stats &tls_stats() {
@@ -37,6 +38,7 @@ hm_tuning tuning() {
   t.share_seeds = g_share_seeds.load(std::memory_order_relaxed);
   t.symmetry = g_symmetry.load(std::memory_order_relaxed);
   t.warps_per_state = g_warps_per_state.load(std::memory_order_relaxed);
+  t.lookahead = g_lookahead.load(std::memory_order_relaxed);
   return t;
 }
 int32_t filter_min() { return g_arc_filter.load(std::memory_order_relaxed); }
@@ -93,7 +95,8 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
       t->leaf_flatten < -1 || t->leaf_flatten > 1 || t->arc_filter < -1 || t->share_seeds < -1 ||
       t->share_seeds > 1 || t->symmetry < -1 || t->symmetry > 1 ||
       (t->warps_per_state != 0 && t->warps_per_state != 1 && t->warps_per_state != 2 &&
-       t->warps_per_state != 4))
+       t->warps_per_state != 4) ||
+      t->lookahead < -1 || t->lookahead > 1)
     return HM_ERR_ARG;
   hm::g_min_blocks.store(mb);
   hm::g_split_min.store(sm);
@@ -105,6 +108,7 @@ extern "C" hm_status hm_set_tuning(const hm_tuning *t) {
   hm::g_share_seeds.store(t->share_seeds < 0 ? -1 : 1);
   hm::g_symmetry.store(t->symmetry < 0 ? -1 : 1);
   hm::g_warps_per_state.store(t->warps_per_state);
+  hm::g_lookahead.store(t->lookahead > 0 ? 1 : -1);
   return HM_OK;
 }
 

@@ -199,9 +199,12 @@ __global__ void k_unpack_rows(const int32_t *__restrict__ packed, const unsigned
   }
 }
 
+// fit (may be NULL): instead of failing with HM_ERR_CAPACITY when some
+// pattern's rows exceed its region, return every count, sort the rows of the
+// patterns that fit and flag them (fit[i] = 1); the others' rows are not valid.
 hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int32_t *modes,
                     int32_t npat, int32_t *rows, const uint64_t *row_offsets, uint64_t *counts,
-                    cudaStream_t s) {
+                    cudaStream_t s, uint8_t *fit = nullptr) {
   if (!g || npat < 0 || (npat > 0 && (!pats || !modes || !counts))) return HM_ERR_ARG;
   if (npat == 0) return HM_OK;
   const bool want_rows = rows != nullptr || row_offsets != nullptr;
@@ -298,6 +301,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   uint32_t launches = 0;
 
   // ---- edge scan: count, size, write
+  NvtxRange r_edge("hm.batch_edge_scan");
   Timer t_edge(s, timing);
   const int grid_e = (int)std::max<int64_t>(1, std::min<int64_t>((m + kSeedThreads - 1) / kSeedThreads,
                                                                    (int64_t)sms * 8));
@@ -367,6 +371,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   A.poll_mask = (uint32_t)tu.poll_every - 1u;
   A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
   A.wps_shift = wps_shift(tu);
+  A.lookahead = tu.lookahead > 0 ? 1 : 0;
   A.seeds = seeds;
   A.nseeds = nseeds;
   A.qbuf = qbuf;
@@ -393,6 +398,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   if (grid <= 0) return HM_ERR_CUDA;
   st.extend_grid = grid;
   st.extend_block = kExtThreads;
+  NvtxRange r_ext("hm.batch_extend");
   Timer t_ext(s, timing);
   extend_kernel<true>(want_rows, counters, slot, false, sym)<<<grid, kExtThreads, smem, s>>>(G, plans[0], A);
   launches += 1;
@@ -425,13 +431,18 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   st.matches = total;
   st.kernel_launches = launches;
   if (!want_rows) return HM_OK;
-  if (over) return HM_ERR_CAPACITY;
-  if (total == 0) return HM_OK;
-
-  // ---- one sort for all patterns: key (pattern id, row), then back to each region
-  Timer t_sort(s, timing);
+  if (over && !fit) return HM_ERR_CAPACITY;
+  // ---- one sort for all patterns whose rows fit: key (pattern id, row), then back to each region
   std::vector<unsigned long long> start(npat + 1, 0);
-  for (int32_t i = 0; i < npat; ++i) start[i + 1] = start[i] + hc[i];
+  for (int32_t i = 0; i < npat; ++i) {
+    const bool ok = hc[i] <= cap[i];
+    if (fit) fit[i] = ok ? 1 : 0;
+    start[i + 1] = start[i] + (ok ? hc[i] : 0);
+  }
+  total = start[npat];
+  if (total == 0) return HM_OK;
+  NvtxRange r_sort("hm.batch_sort_rows");
+  Timer t_sort(s, timing);
   HM_CUDA_TRY(cudaMemcpyAsync(d_start, start.data(), sizeof(unsigned long long) * npat,
                               cudaMemcpyHostToDevice, s));
   const int width = kmax + 1;
@@ -462,6 +473,15 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
 }
 
 }  // namespace
+}  // namespace hm
+
+namespace hm {
+hm_status enumerate_batch_fit(const hm_graph *g, const hm_pattern *const *patterns, const int32_t *modes,
+                              int32_t npat, int32_t *rows_dev, const uint64_t *row_offsets, uint64_t *counts,
+                              uint8_t *fit, cudaStream_t stream) {
+  if (npat > 0 && (!rows_dev || !row_offsets || !fit)) return HM_ERR_ARG;
+  return run_batch(g, patterns, modes, npat, rows_dev, row_offsets, counts, stream, fit);
+}
 }  // namespace hm
 
 extern "C" hm_status hm_count_batch(const hm_graph *g, const hm_pattern *const *patterns,
@@ -506,16 +526,18 @@ std::vector<Dim> tune_dims() {
       {&hm_tuning::poll_every, {32, 128, 512}},
       {&hm_tuning::pair_mode, {0, 1}},
       {&hm_tuning::leaf_flatten, {1, -1}},
+      {&hm_tuning::lookahead, {-1, 1}},
   };
 }
 
 const char *kTuneFields[] = {"extend_min_blocks", "split_min", "pair_mode", "seeds_per_fetch", "poll_every",
-                             "leaf_flatten", "arc_filter", "share_seeds", "symmetry", "warps_per_state"};
+                             "leaf_flatten", "arc_filter", "share_seeds", "symmetry", "warps_per_state",
+                             "lookahead"};
 int32_t hm_tuning::*const kTuneMembers[] = {
     &hm_tuning::extend_min_blocks, &hm_tuning::split_min, &hm_tuning::pair_mode, &hm_tuning::seeds_per_fetch,
     &hm_tuning::poll_every, &hm_tuning::leaf_flatten, &hm_tuning::arc_filter, &hm_tuning::share_seeds,
-    &hm_tuning::symmetry, &hm_tuning::warps_per_state};
-constexpr int kNumTuneFields = 10;
+    &hm_tuning::symmetry, &hm_tuning::warps_per_state, &hm_tuning::lookahead};
+constexpr int kNumTuneFields = 11;
 
 // A fingerprint of the graph (sizes, directory sizes and a strided sample of
 // its sorted arc arrays, FNV-1a) and of the workload (the multiset of pattern

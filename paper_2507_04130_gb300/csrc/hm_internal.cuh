@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "hipermotif.h"
@@ -76,6 +77,15 @@ struct Cons {
   int32_t lab;
 };
 
+// One look-ahead class of a position (see Plan::la).
+struct LookClass {
+  int8_t kind;   // kOut: arcs f(p) -> later positions; kIn: arcs from them
+  int8_t need;   // later positions in the class
+  int16_t pad;
+  int32_t alab;  // arc label
+  int32_t vlab;  // the later positions' vertex label
+};
+
 // Per-pattern, per-mode plan, indexed by position after Alg. 1.
 struct Plan {
   int32_t k;
@@ -117,6 +127,12 @@ struct Plan {
   uint32_t sym_gt[kMaxK];
   uint32_t sym_lt[kMaxK];
   int8_t aut[kMaxAut][kMaxK];
+  // Look-ahead (a labelled form of VF2's terminal-set rules): a candidate for
+  // position p needs, for each class (direction, arc label, neighbour label)
+  // of the pattern arcs between p and later positions, at least `need`
+  // neighbours of that class -- their images must be distinct.
+  int32_t nla[kMaxK];
+  LookClass la[kMaxK][kMaxCons];
 };
 
 // A plan without symmetry breaking: every map is searched for itself.
@@ -282,6 +298,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 namespace hm {
 int32_t filter_min();  // current search length above which the arc filter is probed first
+
+// A named range on the host thread's timeline around the launches of one
+// phase (NVTX): profilers can select a phase's kernels by it ("ncu --nvtx
+// --nvtx-include hm.extend/"); without a tool attached it costs a few ns.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 }
 
 struct hm_graph {
@@ -351,6 +377,13 @@ int radix_sort_launches(int total_bits);
 
 // out[i] = in[0] + ... + in[i-1] for i in [0, n); values and total below 2^32.
 hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t stream);
+
+// Batched enumeration that keeps what fits (the query server's single pass):
+// every count, and for each pattern whose count fits its region [row_offsets[i],
+// row_offsets[i+1]) its sorted rows there and fit[i] = 1; fit[i] = 0 otherwise.
+hm_status enumerate_batch_fit(const hm_graph *g, const hm_pattern *const *patterns, const int32_t *modes,
+                              int32_t npat, int32_t *rows_dev, const uint64_t *row_offsets, uint64_t *counts,
+                              uint8_t *fit, cudaStream_t stream);
 
 int bits_for(int64_t n);  // bits needed for values in [0, n)
 int num_sms();

@@ -125,7 +125,7 @@ struct ExtArgs {
   const unsigned long long *row_cap;  // rows each pattern may write
   unsigned long long *row_cursor;     // rows each pattern has claimed
   int32_t grp_slots;                  // group slots per warp (max over the patterns)
-  int32_t pad2;
+  int32_t lookahead;                  // apply the look-ahead classes at inner depths
   // shared position-0 states (single-pattern launches with P.defer1): one
   // int4 {u, first, end, 0} per distinct position-0 image instead of `seeds`,
   // and the seeds sorted by (u, v), whose .y over [first, end) are the
@@ -488,6 +488,32 @@ __device__ __noinline__ void write_match_rows(const Plan &P, int32_t *row_base, 
       row[v] = i < nmapped ? map[i] : (i == nmapped ? e1 : e2);
     }
   }
+}
+
+// Look-ahead: candidate c for position p has, in every class of P.la[p]
+// (direction, arc label, neighbour label), at least as many neighbours as
+// the later positions of that class need -- their images must be distinct
+// neighbours of c.  Out of line: only the look-ahead knob uses it.
+template <bool kC>
+__device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int p, int32_t c, uint64_t &ctr) {
+  if (kC) ctr += 16;
+  const int4 vd = __ldg(&G.vdir[c]);
+  for (int j = 0; j < P.nla[p]; ++j) {
+    const LookClass lc = P.la[p][j];
+    const int4 *dir = lc.kind == kOut ? G.gdir_out : G.gdir_in;
+    const int32_t first = lc.kind == kOut ? vd.x : vd.z, cnt = lc.kind == kOut ? vd.y : vd.w;
+    int32_t len = 0;
+    for (int32_t e = 0; e < cnt; ++e) {
+      if (kC) ctr += 16;
+      const int4 ent = __ldg(dir + first + e);
+      if (ent.x == lc.alab && ent.y == lc.vlab) {
+        len = ent.w - ent.z;
+        break;
+      }
+    }
+    if (len < lc.need) return false;
+  }
+  return true;
 }
 
 // Find the group (arc label, vertex label) in a directory span; {first, length} or {0, 0}.
@@ -1518,6 +1544,11 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
             }
             ok = check_candidate<kC, kSym>(G, P, S, grp, level, drive, c, leaf, A.root_mask, ctr);
           }
+          m = __ballot_sync(kFull, ok);
+        }
+        if (A.lookahead && level <= k - 3 && P.nla[level] && m) {
+          // look-ahead on the survivors of an inner depth
+          ok = ok && lookahead_ok<kC>(G, P, level, c, ctr);
           m = __ballot_sync(kFull, ok);
         }
         if (lane == 0) S.lo[level] = lo + take;

@@ -111,6 +111,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   Timer t_edge(s, timing);
   const int64_t e_begin = part_start(m, part, nparts), e_end = part_start(m, part + 1, nparts);
   {
+    NvtxRange r_edge("hm.edge_scan");
     int64_t groups = (e_end - e_begin + 3) / 4;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + kSeedThreads - 1) / kSeedThreads,
                                                            (int64_t)sms * 8));
@@ -130,6 +131,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   const unsigned long long *nseeds = &ctl->nseeds_raw;
   Timer t_ov(s, timing && plan.ov_need > 0);
   if (plan.ov_need > 0) {
+    NvtxRange r_ov("hm.overlap_test");
     if (counters)
       k_seed_overlap<true><<<sms * 8, kSeedThreads, 0, s>>>(G, plan.ov_need, seeds_a, &ctl->nseeds_raw,
                                                             seeds_b, (unsigned long long)m, &ctl->nseeds,
@@ -164,6 +166,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   const int4 *groups = nullptr;
   Timer t_grp(s, timing && share);
   if (share) {
+    NvtxRange r_grp("hm.group_seeds");
     unsigned long long ns = 0;
     HM_CUDA_TRY(cudaMemcpyAsync(&ns, nseeds, sizeof(ns), cudaMemcpyDeviceToHost, s));
     HM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -198,6 +201,8 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   // a4 + a5: state injection and extension
   const bool rows = want == Want::kRows;
   Timer t_ext(s, timing && p->k > 2);
+  {  // the extension's launches
+  NvtxRange r_ext("hm.extend");
   if (p->k == 2) {
     k_seed_rows<<<sms * 4, 256, 0, s>>>(plan, seeds, nseeds, rows ? out : nullptr, cap, ctl);
     ++launches;
@@ -231,6 +236,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     A.poll_mask = (uint32_t)tu.poll_every - 1u;
     A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
     A.wps_shift = wps_shift(tu, share);
+    A.lookahead = tu.lookahead > 0 ? 1 : 0;
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
     const bool sym = plan.naut > 1;
@@ -242,6 +248,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     ++launches;
     t_ext.stop();
     HM_CUDA_TRY(cudaGetLastError());
+  }
   }
   Ctl h;
   HM_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -269,6 +276,7 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   if (!rows) return HM_OK;
   if (h.count > cap) return HM_ERR_CAPACITY;
   if (h.count > 1) {
+    NvtxRange r_sort("hm.sort_rows");
     Timer t(s, timing);
     int32_t *tmp;
     HM_CUDA_TRY(sc.get((void **)&tmp, sizeof(int32_t) * (size_t)h.count * p->k));
@@ -461,6 +469,7 @@ extern "C" hm_status hm_count_matches_static(const hm_graph *g, const hm_pattern
     A.poll_mask = (uint32_t)tu.poll_every - 1u;
     A.leaf_flatten = tu.leaf_flatten > 0 ? 1 : 0;
     A.wps_shift = wps_shift(tu);
+    A.lookahead = tu.lookahead > 0 ? 1 : 0;
     const int slot = min_blocks_slot(tu.extend_min_blocks);
     const size_t smem = warp_smem_bytes(plan.ngrp) * kExtWarps;
     const bool sym = plan.naut > 1;

@@ -156,6 +156,24 @@ void build_plan(const PatternGraph &P, const int32_t *order, int induced, hm::Pl
     pl.ncons[p] = c;
   }
   pl.ngrp = slots;
+  // look-ahead classes: the pattern arcs from each position to later ones
+  for (int p = 0; p < k; ++p) {
+    int n = 0;
+    for (int w = p + 1; w < k; ++w)
+      for (int dir = 0; dir < 2; ++dir) {
+        const bool arc = dir == 0 ? A[p][w] : A[w][p];
+        if (!arc) continue;
+        const int32_t alab = dir == 0 ? L[p][w] : L[w][p];
+        const int32_t vl = P.vlab[order[w]];
+        int c = 0;
+        while (c < n && !(pl.la[p][c].kind == (dir == 0 ? hm::kOut : hm::kIn) && pl.la[p][c].alab == alab &&
+                          pl.la[p][c].vlab == vl))
+          ++c;
+        if (c == n) pl.la[p][n++] = hm::LookClass{(int8_t)(dir == 0 ? hm::kOut : hm::kIn), 0, 0, alab, vl};
+        pl.la[p][c].need++;
+      }
+    pl.nla[p] = n;
+  }
 }
 
 // ---- symmetry breaking ---------------------------------------------------------

@@ -110,7 +110,8 @@ def test_graph_load_rejects_bad_arguments_before_the_device(hm):
                                  dict(seeds_per_fetch=5000), dict(poll_every=3),
                                  dict(poll_every=1 << 17), dict(leaf_flatten=2), dict(arc_filter=-2),
                                  dict(share_seeds=2), dict(symmetry=2), dict(symmetry=-2),
-                                 dict(warps_per_state=3), dict(warps_per_state=8), dict(warps_per_state=-1)])
+                                 dict(warps_per_state=3), dict(warps_per_state=8), dict(warps_per_state=-1),
+                                 dict(lookahead=2), dict(lookahead=-2)])
 def test_tuning_rejects_bad_values(hm, bad):
     before = hm.get_tuning()
     with pytest.raises(hm.HMError) as ei:
@@ -123,14 +124,14 @@ def test_tuning_defaults_roundtrip(hm):
     hm.set_tuning(extend_min_blocks=6, split_min=128, pair_mode=1, seeds_per_fetch=4, poll_every=8)
     assert hm.get_tuning() == dict(extend_min_blocks=6, split_min=128, pair_mode=1, seeds_per_fetch=4,
                                    poll_every=8, leaf_flatten=1, arc_filter=1, share_seeds=1, symmetry=1,
-                                   warps_per_state=0)
+                                   warps_per_state=0, lookahead=-1)
     hm.set_tuning(leaf_flatten=-1, arc_filter=-1, symmetry=-1)
     assert hm.get_tuning()["leaf_flatten"] == -1 and hm.get_tuning()["arc_filter"] == -1
     assert hm.get_tuning()["symmetry"] == -1
     hm.set_tuning()
     assert hm.get_tuning() == dict(extend_min_blocks=4, split_min=64, pair_mode=0, seeds_per_fetch=1,
                                    poll_every=128, leaf_flatten=1, arc_filter=1, share_seeds=1, symmetry=1,
-                                   warps_per_state=0)
+                                   warps_per_state=0, lookahead=-1)
 
 
 def _bfs_order(k, src, dst):

@@ -408,7 +408,9 @@ def test_instrumented_kernels_agree_and_count_bytes(hm):
                                    dict(arc_filter=1, leaf_flatten=-1, pair_mode=1),
                                    dict(warps_per_state=2), dict(warps_per_state=4, seeds_per_fetch=3),
                                    dict(warps_per_state=4, leaf_flatten=-1, split_min=2),
-                                   dict(warps_per_state=2, symmetry=-1, arc_filter=-1)])
+                                   dict(warps_per_state=2, symmetry=-1, arc_filter=-1),
+                                   dict(lookahead=1), dict(lookahead=1, pair_mode=1, split_min=2),
+                                   dict(lookahead=1, leaf_flatten=-1, warps_per_state=2)])
 def test_tuning_knobs_never_change_results(hm, knobs):
     g0 = synth.config3_graph(n=2000, n_unique=60_000, n_recip=3000)
     g = synth.Graph(g0.n, g0.src, g0.dst, (g0.vlab % 2).astype(np.int32), g0.elab % 2)

@@ -95,10 +95,15 @@ def test_server_matches_the_oracle_on_a_small_graph(hm):
         srv.close()
 
 
+# what the server charges: 24 B per target arc whose labels fit the query's
+# seeding arc (every arc, with one vertex and one arc label), and 12 MiB per batch
+BATCH_FIXED = 12 << 20
+
+
 def test_admission_by_memory_budget_and_dropped_rows(hm):
     g = synth.er_graph(2000, 30000, 1, 1, seed=3)
     G = hm.Graph.from_synth(g)
-    per_query = 24 * g.m + (8 << 20)
+    per_query = 24 * g.m + BATCH_FIXED
     p = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
                       np.zeros(3, np.int32), np.zeros(2, np.int32), "path3")
     P = hm.Pattern.from_synth(p)
@@ -116,7 +121,27 @@ def test_admission_by_memory_budget_and_dropped_rows(hm):
     finally:
         srv.close()
     with pytest.raises(hm.HMError):
-        hm.Server(G, slots=1, max_batch=1, mem_budget=per_query - 1)
+        hm.Server(G, slots=1, max_batch=1, mem_budget=BATCH_FIXED - 1)
+
+
+def test_admission_charges_each_query_by_its_seeding_arc(hm):
+    """Queries whose seeding arc fits few target arcs are admitted together under a budget
+    that holds only one query whose seeding arc fits every arc."""
+    g = synth.er_graph(3000, 40000, 4, 1, seed=5)
+    G = hm.Graph.from_synth(g)
+    few = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
+                        np.array([0, 1, 2], np.int32), np.zeros(2, np.int32), "labelled_path3")
+    # a flat charge of 24 B x m + 8 MiB per query would admit two of them per batch
+    srv = hm.Server(G, slots=1, max_batch=8, mem_budget=BATCH_FIXED + 24 * g.m // 2 + (8 << 20))
+    try:
+        ids = [srv.submit(few, hm.MONO, want_rows=True) for _ in range(8)]
+        want = hm.count_matches(G, hm.Pattern.from_synth(few), hm.MONO)
+        for qid in ids:
+            r = srv.result(qid)
+            assert r["count"] == want and not r["rows_dropped"]
+        assert srv.stats()["batches"] <= 3   # each needs ~1/16 of the arcs: they share batches
+    finally:
+        srv.close()
 
 
 def test_batches_overlap_on_the_device(hm):
@@ -138,7 +163,7 @@ def test_batches_overlap_on_the_device(hm):
 def test_close_drains_queries_still_waiting_for_memory(hm):
     g = synth.er_graph(2000, 30000, 1, 1, seed=4)
     G = hm.Graph.from_synth(g)
-    per_query = 24 * g.m + (8 << 20)
+    per_query = 24 * g.m + BATCH_FIXED
     p = synth.Pattern(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32),
                       np.zeros(3, np.int32), np.zeros(2, np.int32), "path3")
     # three slots but memory for one query: most queries wait for memory when close() is called
