@@ -500,14 +500,24 @@ typedef struct {
   int32_t extend_block;     /* threads per block                            */
   uint32_t kernel_launches; /* kernels the call launched                    */
   uint32_t pad;
-  /* algorithmic bytes each kernel requested (loads and stores the method
-   * needs, counted per access); filled only while counters are enabled */
+  /* bytes each kernel's accesses requested, at the granularity it reads
+   * them (a 32-byte filter block per probe, a 16-byte vertex record, ...);
+   * filled only while counters are enabled */
   uint64_t bytes_edge_scan;
   uint64_t bytes_overlap;
   uint64_t bytes_extend;
   uint64_t candidates;      /* candidate vertices examined by the extension */
   uint64_t level_chunks[HM_MAX_K];     /* 32-candidate chunks per depth (counters only) */
   uint64_t level_candidates[HM_MAX_K]; /* candidates per depth (counters only)          */
+  /* the same kernels' bytes under the method's cost model (counters only):
+   * 12 B per arc scanned and per vertex record gathered, 8 B per candidate
+   * read (neighbour + arc label), ceil(log2(d+1)) x 4 B per membership or
+   * non-arc test over the shorter list (d entries), 4 B per surviving
+   * candidate's label, 4 B per neighbour merged by the overlap test, 8 B per
+   * state and 4k B per row written */
+  uint64_t model_bytes_edge_scan;
+  uint64_t model_bytes_overlap;
+  uint64_t model_bytes_extend;
 } hm_stats;
 
 hm_status hm_last_stats(hm_stats *out);

@@ -53,6 +53,9 @@ class hm_stats(ctypes.Structure):
         ("candidates", ctypes.c_uint64),
         ("level_chunks", ctypes.c_uint64 * HM_MAX_K),
         ("level_candidates", ctypes.c_uint64 * HM_MAX_K),
+        ("model_bytes_edge_scan", ctypes.c_uint64),
+        ("model_bytes_overlap", ctypes.c_uint64),
+        ("model_bytes_extend", ctypes.c_uint64),
     ]
 
     def as_dict(self):

@@ -51,7 +51,7 @@ __device__ __forceinline__ bool seed_test_batch(const DevGraph &G, const Plan &P
   if (iv.y < P.dout[1] || iv.z < P.din[1]) return false;
   if (P.back_req | P.back_forbid) {
     int32_t lab = 0;
-    uint64_t unused = 0;
+    Bytes unused;
     const bool found = arc_lookup<false>(G, b, a, ib.y, ia.z, &lab, unused);
     if (P.back_req && (!found || lab != P.back_lab)) return false;
     if (P.back_forbid && found) return false;
@@ -418,6 +418,7 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
   st.tasks_donated = h.donated;
   st.chunks = h.chunks;
   st.bytes_extend = h.bytes_extend;
+  st.model_bytes_extend = h.bytes_extend_model;
   st.candidates = h.lanes;
   if (h.status == kStatBudget) return HM_ERR_BUDGET;
   if (h.status != kStatOk) return HM_ERR_CUDA;

@@ -145,6 +145,34 @@ inline void strip_symmetry(Plan &P) {
 // Budget / status words shared by all warps of one call.
 enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
 
+// Byte tallies of the instrumented kernel variants (hm_set_counters): `req`,
+// the bytes the kernel's accesses request at the granularity it reads them
+// (a 32-byte filter block per filter probe, a 16-byte vertex record, ...);
+// `model`, the method's algorithmic bytes under the survey's cost model: 12 B
+// per arc scanned, 12 B per vertex record gathered (label and two degrees),
+// 8 B per candidate read from an adjacency list (neighbour and arc label),
+// ceil(log2(d+1)) x 4 B per membership or non-arc test (a binary search of
+// the shorter list, d entries), 4 B per surviving candidate's label, 4 B per
+// neighbour merged by the overlap test, 8 B per state and 4k B per row
+// written.  `c += b` adds to req.
+struct Bytes {
+  uint64_t req = 0, model = 0;
+  __host__ __device__ Bytes &operator+=(uint64_t b) {
+    req += b;
+    return *this;
+  }
+};
+
+// ceil(log2(d + 1)) x 4: the bytes of a binary search over d sorted entries.
+__host__ __device__ __forceinline__ uint64_t search_bytes(int64_t d) {
+  uint64_t b = 0;
+  while (d > 0) {
+    d >>= 1;
+    b += 4;
+  }
+  return b;
+}
+
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
@@ -154,7 +182,7 @@ enum : int32_t { kStatOk = 0, kStatBudget = 1, kStatQueue = 2 };
 // 32-bit (the loader caps m below 2^31).  kCount adds the bytes read to `bytes`.
 template <bool kCount>
 __device__ __forceinline__ int32_t search_c(const int32_t *__restrict__ a, int32_t lo, int32_t len,
-                                            int32_t x, uint64_t &bytes) {
+                                            int32_t x, Bytes &bytes) {
   const int32_t end = lo + len;
   while (len > 0) {
     const int32_t half = len >> 1;
@@ -219,7 +247,7 @@ __host__ __device__ __forceinline__ uint64_t labelled_key(uint64_t pair, int32_t
 }
 
 template <bool kCount>
-__device__ __forceinline__ bool filter_has(const DevGraph &G, uint64_t h, uint64_t &bytes) {
+__device__ __forceinline__ bool filter_has(const DevGraph &G, uint64_t h, Bytes &bytes) {
   const FilterSlot f = filter_slot_of(h, G.afilt_nblk);
   const uint4 a = __ldg(G.afilt + 2 * (size_t)f.blk);
   const uint4 b = __ldg(G.afilt + 2 * (size_t)f.blk + 1);
@@ -233,7 +261,7 @@ __device__ __forceinline__ bool filter_has(const DevGraph &G, uint64_t h, uint64
 
 // false: there is certainly no arc u -> v.  true: there may be.
 template <bool kCount>
-__device__ __forceinline__ bool arc_maybe(const DevGraph &G, int32_t u, int32_t v, uint64_t &bytes) {
+__device__ __forceinline__ bool arc_maybe(const DevGraph &G, int32_t u, int32_t v, Bytes &bytes) {
   return filter_has<kCount>(G, pair_key(u, v), bytes);
 }
 
@@ -250,7 +278,7 @@ __host__ __device__ __forceinline__ uint32_t hash_bucket(uint64_t pair, uint32_t
 // Is u -> v an arc?  If so, *lab is its label.
 template <bool kCount>
 __device__ __forceinline__ bool arc_find(const DevGraph &G, int32_t u, int32_t v, int32_t *lab,
-                                         uint64_t &bytes) {
+                                         Bytes &bytes) {
   uint32_t b = hash_bucket(pair_key(u, v), G.ahash_nbkt);
   for (uint32_t it = 0; it < G.ahash_nbkt; ++it) {
     const int4 s0 = __ldg(G.ahash + 2 * (size_t)b);
@@ -273,7 +301,7 @@ __device__ __forceinline__ bool arc_find(const DevGraph &G, int32_t u, int32_t v
 // false: there is certainly no arc u -> v with label lab.  true: there may be.
 template <bool kCount>
 __device__ __forceinline__ bool arc_maybe_l(const DevGraph &G, int32_t u, int32_t v, int32_t lab,
-                                            uint64_t &bytes) {
+                                            Bytes &bytes) {
   return filter_has<kCount>(G, labelled_key(pair_key(u, v), lab), bytes);
 }
 

@@ -90,9 +90,10 @@ struct Ctl {
   unsigned long long rows_written;
   unsigned long long chunks;
   unsigned long long donated;
-  unsigned long long bytes_edge;              // algorithmic bytes (instrumented launches only)
-  unsigned long long bytes_overlap;
-  unsigned long long bytes_extend;
+  // bytes of the instrumented launches: {requested, model} for each kernel
+  unsigned long long bytes_edge, bytes_edge_model;
+  unsigned long long bytes_overlap, bytes_overlap_model;
+  unsigned long long bytes_extend, bytes_extend_model;
   unsigned long long lanes;                   // candidates examined (instrumented launches only)
   unsigned long long level_chunks[kMaxK];     // per depth (instrumented launches only)
   unsigned long long level_lanes[kMaxK];
@@ -151,7 +152,7 @@ __device__ __forceinline__ bool use_filter(const DevGraph &G, int32_t len) {
 // ---------------------------------------------------------------------------
 template <bool kC>
 __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t y, int32_t outdeg_x,
-                                           int32_t indeg_y, int32_t *lab, uint64_t &ctr) {
+                                           int32_t indeg_y, int32_t *lab, Bytes &ctr) {
   if (outdeg_x == 0 || indeg_y == 0) return false;
   if (use_filter(G, min(outdeg_x, indeg_y)))
     return arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, lab, ctr);
@@ -180,14 +181,18 @@ __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t
 template <bool kC>
 __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int32_t a, int32_t b,
                                           int32_t l, const uint8_t *root_mask, int2 *out,
-                                          uint64_t &ctr, bool fresh = true) {
+                                          Bytes &ctr, bool fresh = true) {
   if (l != P.seed_lab) return false;                       // match(e1, e2)
   const int32_t u = P.seed_rev ? b : a;                     // image of position 0
   const int32_t v = P.seed_rev ? a : b;                     // image of position 1
   if (kC && (fresh || P.seed_rev)) ctr += 16;
+  if (kC) ctr.model += 12;
   const int4 iu = __ldg(&G.vi[u]);                          // Alg. 2 on u
   if (iu.x != P.vlab[0] || iu.y < P.dout[0] || iu.z < P.din[0]) return false;
-  if (kC) ctr += 16;
+  if (kC) {
+    ctr += 16;
+    ctr.model += 12;
+  }
   const int4 iv = __ldg(&G.vi[v]);                          // match(v, 1) + degrees
   if (iv.x != P.vlab[1] || iv.y < P.dout[1] || iv.z < P.din[1]) return false;
   if (root_mask && ((P.root_pos == 0 && !root_mask[u]) || (P.root_pos == 1 && !root_mask[v])))
@@ -196,6 +201,7 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
     // the arc opposite to the seeding one is (b -> a) in both seeding directions
     const int4 ib = P.seed_rev ? iu : iv;
     const int4 ia = P.seed_rev ? iv : iu;
+    if (kC) ctr.model += search_bytes(min(ib.y, ia.z));
     if (P.back_req && use_filter(G, min(ib.y, ia.z)) && !arc_maybe_l<kC>(G, b, a, P.back_lab, ctr))
       return false;
     int32_t lab = 0;
@@ -204,7 +210,10 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
     if (P.back_forbid && found) return false;
   }
   *out = make_int2(u, v);
-  if (kC) ctr += 8;
+  if (kC) {
+    ctr += 8;
+    ctr.model += 8;
+  }
   return true;
 }
 
@@ -226,7 +235,7 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
             const uint8_t *__restrict__ root_mask, int2 *__restrict__ seeds,
             unsigned long long cap, unsigned long long *__restrict__ nseeds,
             unsigned long long *__restrict__ bytes, int64_t e_begin, int64_t e_end) {
-  uint64_t ctr = 0;
+  Bytes ctr;
   __shared__ int2 s_buf[kSeedThreads / 32][kSeedBuf];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int2 *buf = s_buf[warp];
@@ -262,7 +271,10 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     if (gi >= g_end) {
       // past this warp's span
     } else if (gi < full_groups) {
-      if (kC) ctr += 48;
+      if (kC) {
+        ctr += 48;
+        ctr.model += 48;
+      }
       ok[0] = seed_test<kC>(G, P, a.x, b.x, l.x, root_mask, &s[0], ctr);
       ok[1] = seed_test<kC>(G, P, a.y, b.y, l.y, root_mask, &s[1], ctr, a.y != a.x);
       ok[2] = seed_test<kC>(G, P, a.z, b.z, l.z, root_mask, &s[2], ctr, a.z != a.y);
@@ -270,7 +282,10 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
     } else if (gi < ngroups) {
       for (int j = 0; j < 4; ++j) {
         const int64_t e = e_begin + gi * 4 + j;
-        if (kC && e < e_end) ctr += 12;
+        if (kC && e < e_end) {
+          ctr += 12;
+          ctr.model += 12;
+        }
         if (e < e_end)
           ok[j] = seed_test<kC>(G, P, G.src[e], G.out_adj[e], G.out_elab[e], root_mask, &s[j], ctr);
       }
@@ -306,8 +321,12 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
       if (off + i < cap) seeds[off + i] = buf[i];
   }
   if (kC) {
-    for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
-    if (lane == 0 && ctr) atomicAdd(bytes, (unsigned long long)ctr);
+    for (int o = 16; o; o >>= 1) {
+      ctr.req += __shfl_xor_sync(kFull, ctr.req, o);
+      ctr.model += __shfl_xor_sync(kFull, ctr.model, o);
+    }
+    if (lane == 0 && ctr.req) atomicAdd(bytes, (unsigned long long)ctr.req);
+    if (lane == 0 && ctr.model) atomicAdd(bytes + 1, (unsigned long long)ctr.model);
   }
 }
 
@@ -318,7 +337,7 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
 // Is w a neighbour (in or out) of y?
 template <bool kC>
 __device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, int2 oy,
-                                        int32_t w, uint64_t &ctr) {
+                                        int32_t w, Bytes &ctr) {
   int32_t lab;
   if (iy.y && (use_filter(G, iy.y) ? arc_maybe<kC>(G, y, w, ctr) && arc_find<kC>(G, y, w, &lab, ctr)
                                    : search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0))
@@ -336,7 +355,7 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
                unsigned long long cap, unsigned long long *__restrict__ nout,
                unsigned long long *__restrict__ bytes, const Plan *__restrict__ plans = nullptr,
                const int32_t *__restrict__ pid_in = nullptr, int32_t *__restrict__ pid_out = nullptr) {
-  uint64_t ctr = 0;
+  Bytes ctr;
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -347,6 +366,7 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
     const int32_t need = kB ? plans[pid].ov_need : need_all;
     if (kC && lane == 0) ctr += 72;
     int4 iu = __ldg(&G.vi[uv.x]), iv = __ldg(&G.vi[uv.y]);
+    if (kC && lane == 0) ctr.model += 24 + 4ull * (iu.y + iu.z + iv.y + iv.z);  // a merge of the four lists
     int2 ou = __ldg(&G.off[uv.x]), ov = __ldg(&G.off[uv.y]);
     // iterate the side with fewer incident arcs, probe the other
     const bool swap = (iu.y + iu.z) > (iv.y + iv.z);
@@ -381,12 +401,19 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
         out[at] = uv;
         if (kB) pid_out[at] = pid;
       }
-      if (kC) ctr += 8;
+      if (kC) {
+        ctr += 8;
+        ctr.model += 8;
+      }
     }
   }
   if (kC) {
-    for (int o = 16; o; o >>= 1) ctr += __shfl_xor_sync(kFull, ctr, o);
-    if (lane == 0 && ctr) atomicAdd(bytes, (unsigned long long)ctr);
+    for (int o = 16; o; o >>= 1) {
+      ctr.req += __shfl_xor_sync(kFull, ctr.req, o);
+      ctr.model += __shfl_xor_sync(kFull, ctr.model, o);
+    }
+    if (lane == 0 && ctr.req) atomicAdd(bytes, (unsigned long long)ctr.req);
+    if (lane == 0 && ctr.model) atomicAdd(bytes + 1, (unsigned long long)ctr.model);
   }
 }
 
@@ -436,7 +463,7 @@ struct WarpState {
 
 template <bool kC>
 __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int pos, int32_t c,
-                                           int lane, uint64_t &ctr) {
+                                           int lane, Bytes &ctr) {
   if (kC && lane == 0) ctr += 48;
   // three independent 16-byte loads, each lane writing its own record's fields
   const bool known = c >= 0;  // c < 0: position 1 of a shared position-0 state, not yet chosen
@@ -495,7 +522,7 @@ __device__ __noinline__ void write_match_rows(const Plan &P, int32_t *row_base, 
 // the later positions of that class need -- their images must be distinct
 // neighbours of c.  Out of line: only the look-ahead knob uses it.
 template <bool kC>
-__device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int p, int32_t c, uint64_t &ctr) {
+__device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int p, int32_t c, Bytes &ctr) {
   if (kC) ctr += 16;
   const int4 vd = __ldg(&G.vdir[c]);
   for (int j = 0; j < P.nla[p]; ++j) {
@@ -519,7 +546,7 @@ __device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int 
 // Find the group (arc label, vertex label) in a directory span; {first, length} or {0, 0}.
 template <bool kC>
 __device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t first, int32_t cnt,
-                                           int32_t alab, int32_t vlab, int lane, uint64_t &ctr) {
+                                           int32_t alab, int32_t vlab, int lane, Bytes &ctr) {
   for (int32_t b = 0; b < cnt; b += 32) {
     int4 e = make_int4(0, 0, 0, 0);
     bool hit = false;
@@ -543,7 +570,7 @@ __device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t
 template <bool kC>
 __device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, WarpState &S,
                                             int2 *__restrict__ grp, int p, int lane, bool keep,
-                                            uint64_t &ctr) {
+                                            Bytes &ctr) {
   int best = 0;
   int32_t best_len = INT32_MAX;
   for (int j = 0; j < P.npos[p]; ++j) {
@@ -574,7 +601,7 @@ template <bool kC, bool kSym>
 __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P,
                                                 const WarpState &S, const int2 *__restrict__ grp,
                                                 int p, int drive, int32_t c, bool leaf,
-                                                const uint8_t *root_mask, uint64_t &ctr) {
+                                                const uint8_t *root_mask, Bytes &ctr) {
   for (int i = 0; i < p; ++i)
     if (S.map[i] == c) return false;                        // injective
   if (root_mask && p == P.root_pos && !root_mask[c]) return false;
@@ -604,6 +631,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int2 r = grp[P.gbase[p] + j];
       const int32_t rev_len = fwd ? vi.z : vi.y;
       if (r.y == 0 || rev_len == 0) return false;
+      if (kC) ctr.model += search_bytes(min(rev_len, r.y));
       if (use_filter(G, min(rev_len, r.y))) {
         found = arc_maybe_l<kC>(G, x, y, cs.lab, ctr) && arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab;
       } else if (rev_len < r.y) {
@@ -625,6 +653,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
       const int32_t lb = fwd ? vi.z : vi.y;
       if (la == 0 || lb == 0) continue;
+      if (kC) ctr.model += search_bytes(min(la, lb));
       if (use_filter(G, min(la, lb))) {
         found = arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr);
       } else if (la <= lb) {
@@ -649,7 +678,7 @@ template <bool kC, bool kSym>
 __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const WarpState &S,
                                           const int2 *__restrict__ grp, int p, int j, int32_t c,
                                           bool base, bool leaf, const uint8_t *root_mask,
-                                          uint64_t &ctr) {
+                                          Bytes &ctr) {
   if (base) {
     for (int i = 0; i < p; ++i)
       if (S.map[i] == c) return false;
@@ -669,6 +698,7 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
     const int2 r = grp[P.gbase[p] + j];
     const int32_t rev_len = fwd ? vi.z : vi.y;
     if (r.y == 0 || rev_len == 0) return false;
+    if (kC) ctr.model += search_bytes(min(rev_len, r.y));
     if (use_filter(G, min(rev_len, r.y)))
       return arc_maybe_l<kC>(G, x, y, cs.lab, ctr) && arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab;
     if (rev_len < r.y) {
@@ -685,6 +715,7 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
   const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
   const int32_t lb = fwd ? vi.z : vi.y;
   if (la == 0 || lb == 0) return true;
+  if (kC) ctr.model += search_bytes(min(la, lb));
   if (use_filter(G, min(la, lb))) return !(arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr));
   if (la <= lb)
     return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
@@ -711,7 +742,7 @@ constexpr int32_t kFlatMax = 2048;
 template <bool kC>
 __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &P, const WarpState &S,
                                                  const int2 *__restrict__ grp, int p, int drive, int32_t d,
-                                                 const LeafOwner &o, uint64_t &ctr) {
+                                                 const LeafOwner &o, Bytes &ctr) {
   const int L = p - 1;
   const int nc = P.ncons[p];
   if (kC) ctr += 32;
@@ -730,6 +761,7 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
       const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
       const int32_t rev_len = fwd ? vi.z : vi.y;
       if (r.y == 0 || rev_len == 0) return false;
+      if (kC) ctr.model += search_bytes(min(rev_len, r.y));
       bool found;
       if (rev_len < r.y) {
         const int32_t i = fwd ? search_c<kC>(G.in_adj, od.y, rev_len, fq, ctr)
@@ -745,6 +777,7 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
       const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[q]) : (mine ? o.deg_in : S.deg_in[q]);
       const int32_t lb = fwd ? vi.z : vi.y;
       if (la == 0 || lb == 0) continue;
+      if (kC) ctr.model += search_bytes(min(la, lb));
       const bool found =
           la <= lb ? search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? q_off_out : q_off_in, la, d, ctr) >= 0
                    : search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? od.y : od.x, lb, fq, ctr) >= 0;
@@ -758,7 +791,7 @@ template <bool kC, bool kSym>
 __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, const WarpState &S,
                                            const int2 *__restrict__ grp, int p, int drive, int32_t d,
                                            const LeafOwner &o, const uint8_t *root_mask,
-                                           uint64_t &ctr) {
+                                           Bytes &ctr) {
   const int L = p - 1;
   if (d == o.c) return false;
   for (int i = 0; i < L; ++i)
@@ -780,10 +813,12 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
       if (cs.kind <= kIn) {
         const int2 r = mine ? (cs.kind == kOut ? o.own[0] : o.own[1]) : grp[P.gbase[p] + j];
         if (r.y == 0) return false;
+        if (kC) ctr.model += search_bytes(r.y);
         if (use_filter(G, r.y) && !arc_maybe_l<kC>(G, fwd ? fq : d, fwd ? d : fq, cs.lab, ctr))
           return false;
       } else {
         const int32_t la = fwd ? (mine ? o.deg_out : S.deg_out[cs.q]) : (mine ? o.deg_in : S.deg_in[cs.q]);
+        if (kC) ctr.model += search_bytes(la);
         if (la == 0 || (use_filter(G, la) && !arc_maybe<kC>(G, fwd ? fq : d, fwd ? d : fq, ctr)))
           settled |= 1ull << j;
       }
@@ -837,7 +872,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
 
 // Is there an arc x -> y (any label)?
 template <bool kC>
-__device__ __forceinline__ bool arc_exists(const DevGraph &G, int32_t x, int32_t y, uint64_t &ctr) {
+__device__ __forceinline__ bool arc_exists(const DevGraph &G, int32_t x, int32_t y, Bytes &ctr) {
   int32_t lab;
   if (G.filt_min >= 0) return arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr);
   if (kC) ctr += 32;
@@ -861,7 +896,7 @@ template <bool kRows, bool kC>
 __device__ void expand_position1(const DevGraph &G, const Plan &P, const WarpState &S, const ExtArgs &A,
                                  bool ok, int nmapped, int32_t mL, int32_t mK, int lane,
                                  unsigned long long &task_count, unsigned long long *row_cursor,
-                                 int32_t *row_base, unsigned long long row_cap, uint64_t &ctr) {
+                                 int32_t *row_base, unsigned long long row_cap, Bytes &ctr) {
   const int k = P.k;
   const int32_t vlo = S.vlo, vhi = S.vhi;
   if (!kRows && P.ndefer == 0) {
@@ -895,7 +930,10 @@ __device__ void expand_position1(const DevGraph &G, const Plan &P, const WarpSta
     int32_t v = -1;
     if (live) {
       v = __ldg(&A.sorted_seeds[vlo + vi].y);
-      if (kC) ctr += 8;
+      if (kC) {
+        ctr += 8;
+        ctr.model += 8;
+      }
       good = v != cK && (nmapped == k - 1 || v != cL);
       for (int i = 0; i < nmapped && good; ++i)
         if (S.map[i] == v) good = false;  // injective (S.map[1] = -1)
@@ -916,7 +954,10 @@ __device__ void expand_position1(const DevGraph &G, const Plan &P, const WarpSta
       if (good) {
         const unsigned long long r = at + __popc(bal & lanemask_lt());
         if (r < row_cap) {
-          if (kC) ctr += 4 * k;
+          if (kC) {
+            ctr += 4 * k;
+            ctr.model += 4 * k;
+          }
           int32_t *row = row_base + r * k;
           for (int i = 0; i < k; ++i)
             row[P.orig[i]] = i == 1 ? v : (i < nmapped ? S.map[i] : (i == k - 1 ? cK : cL));
@@ -934,7 +975,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
                                  int2 *__restrict__ grp, int L, const int32_t *__restrict__ adj,
                                  int32_t base, uint32_t m, int lane, const uint8_t *root_mask,
                                  unsigned long long &task_count, Ctl *ctl, uint32_t &chunks,
-                                 uint64_t &ctr) {
+                                 Bytes &ctr) {
   const int p = L + 1;
   const int k = P.k;
   const int npos = P.npos[p];
@@ -1044,7 +1085,10 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
   auto candidate_at = [&](int32_t g, int ow) {
     if (g >= total) return -1;
     const int4 od = S.owner_drive[ow];
-    if (kC) ctr += 4;
+    if (kC) {
+      ctr += 4;
+      ctr.model += 8;
+    }
     return __ldg((od.z == kOut ? G.gout_adj : G.gin_adj) + od.y + (g - od.w));
   };
   // the next chunk's owners and candidates are fetched while this chunk is checked
@@ -1077,14 +1121,20 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
         if (!kSym || P.naut == 1) {
           const unsigned long long r = at + __popc(bal & lanemask_lt());
           if (r < S.row_cap) {
-            if (kC) ctr += 4 * k;
+            if (kC) {
+              ctr += 4 * k;
+              ctr.model += 4 * k;
+            }
             int32_t *row = S.row_base + r * k;
             for (int i = 0; i < L; ++i) row[P.orig[i]] = S.map[i];
             row[P.orig[L]] = oo.c;
             row[P.orig[p]] = d;
           }
         } else {
-          if (kC) ctr += 4ull * k * P.naut;
+          if (kC) {
+            ctr += 4ull * k * P.naut;
+            ctr.model += 4ull * k * P.naut;
+          }
           write_match_rows(P, S.row_base, at + (unsigned long long)__popc(bal & lanemask_lt()) * P.naut,
                            S.row_cap, S.map, L, oo.c, d);
         }
@@ -1323,7 +1373,8 @@ template <bool kRows, bool kC, int kMinBlocks, bool kBatch, bool kShared = false
 __global__ void __launch_bounds__(kExtThreads, kMinBlocks)
 k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
          const __grid_constant__ ExtArgs A) {
-  uint64_t ctr = 0, lanes = 0;
+  Bytes ctr;
+  uint64_t lanes = 0;
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int lane = threadIdx.x & 31;
   const size_t stride = warp_smem_bytes(kBatch ? A.grp_slots : P0.ngrp);
@@ -1377,7 +1428,10 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
         } else {
           const int2 uv = A.seeds[si];
           if (kBatch) pid = A.seed_pid[si];
-          if (kC && lane == 0) ctr += kBatch ? 12 : 8;
+          if (kC && lane == 0) {
+            ctr += kBatch ? 12 : 8;
+            ctr.model += 8;
+          }
           set_mapped<kC>(G, S, 0, uv.x, lane, ctr);
           set_mapped<kC>(G, S, 1, uv.y, lane, ctr);
           // symmetry breaking between positions 0 and 1: the seed is kept by
@@ -1519,6 +1573,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
             const int32_t cc = __ldg(adj + lo + ci);
             if (kC && slot == 0) {
               ctr += 4;
+              ctr.model += 8;
               ++lanes;
             }
             pass = check_one<kC, kSym>(G, P, S, grp, level, slot < drive ? slot : slot + 1, cc, slot == 0,
@@ -1540,12 +1595,14 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
             c = __ldg(adj + idx);
             if (kC) {
               ctr += 4;
+              ctr.model += 8;
               ++lanes;
             }
             ok = check_candidate<kC, kSym>(G, P, S, grp, level, drive, c, leaf, A.root_mask, ctr);
           }
           m = __ballot_sync(kFull, ok);
         }
+        if (kC && ok) ctr.model += 4;  // the survivor's label
         if (A.lookahead && level <= k - 3 && P.nla[level] && m) {
           // look-ahead on the survivors of an inner depth
           ok = ok && lookahead_ok<kC>(G, P, level, c, ctr);
@@ -1574,13 +1631,19 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
             if (ok && (!kSym || P.naut == 1)) {
               const unsigned long long r = at + __popc(m & lanemask_lt());
               if (r < S.row_cap) {
-                if (kC) ctr += 4 * k;
+                if (kC) {
+                  ctr += 4 * k;
+                  ctr.model += 4 * k;
+                }
                 int32_t *row = S.row_base + r * k;
                 for (int i = 0; i < k - 1; ++i) row[P.orig[i]] = S.map[i];
                 row[P.orig[k - 1]] = c;
               }
             } else if (ok) {
-              if (kC) ctr += 4ull * k * P.naut;
+              if (kC) {
+                ctr += 4ull * k * P.naut;
+                ctr.model += 4ull * k * P.naut;
+              }
               write_match_rows(P, S.row_base, at + (unsigned long long)__popc(m & lanemask_lt()) * P.naut,
                                S.row_cap, S.map, k - 1, c, 0);
             }
@@ -1628,11 +1691,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
   }
   if (kC) {
     for (int o = 16; o; o >>= 1) {
-      ctr += __shfl_xor_sync(kFull, ctr, o);
+      ctr.req += __shfl_xor_sync(kFull, ctr.req, o);
+      ctr.model += __shfl_xor_sync(kFull, ctr.model, o);
       lanes += __shfl_xor_sync(kFull, lanes, o);
     }
     if (lane == 0) {
-      atomicAdd(&A.ctl->bytes_extend, (unsigned long long)ctr);
+      atomicAdd(&A.ctl->bytes_extend, (unsigned long long)ctr.req);
+      atomicAdd(&A.ctl->bytes_extend_model, (unsigned long long)ctr.model);
       atomicAdd(&A.ctl->lanes, (unsigned long long)lanes);
     }
   }

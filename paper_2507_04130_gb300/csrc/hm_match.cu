@@ -264,6 +264,9 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
   st.bytes_edge_scan = h.bytes_edge;
   st.bytes_overlap = h.bytes_overlap;
   st.bytes_extend = h.bytes_extend;
+  st.model_bytes_edge_scan = h.bytes_edge_model;
+  st.model_bytes_overlap = h.bytes_overlap_model;
+  st.model_bytes_extend = h.bytes_extend_model;
   st.candidates = h.lanes;
   for (int i = 0; i < kMaxK; ++i) {
     st.level_chunks[i] = h.level_chunks[i];

@@ -396,6 +396,9 @@ def test_instrumented_kernels_agree_and_count_bytes(hm):
     np.testing.assert_array_equal(inst, plain)
     assert st["bytes_edge_scan"] >= 12 * g.m
     assert st["bytes_extend"] > 0 and st["candidates"] > 0
+    # the cost model: 12 B per arc scanned at least; 8 B per candidate read at least
+    assert st["model_bytes_edge_scan"] >= 12 * g.m
+    assert st["model_bytes_extend"] >= 8 * st["candidates"]
 
 
 @pytest.mark.parametrize("knobs", [dict(extend_min_blocks=5), dict(extend_min_blocks=6),
