@@ -455,6 +455,9 @@ struct WarpState {
   // read by the lanes whose candidates they own
   LeafOwner owners[32];
   int4 owner_drive[32];     // {driving condition, range start, its kind, offset in the sweep}
+  int4 owner_probe[32];     // {anchor, flags, arc label, group length}: the owner's first
+                            // other positive condition, tested by the filter before the rest
+                            // (flags: 1 valid, 2 arc anchor -> candidate, condition index << 8)
   Task stage;               // task being donated or received
 };
 // Each warp's WarpState is followed in shared memory by one int2 per positive
@@ -787,10 +790,12 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
   return true;
 }
 
+// `first`: a positive condition whose filter probe the caller has already
+// passed (-1: none); its exact lookup still follows.
 template <bool kC, bool kSym>
 __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, const WarpState &S,
-                                           const int2 *__restrict__ grp, int p, int drive, int32_t d,
-                                           const LeafOwner &o, const uint8_t *root_mask,
+                                           const int2 *__restrict__ grp, int p, int drive, int first,
+                                           int32_t d, const LeafOwner &o, const uint8_t *root_mask,
                                            Bytes &ctr) {
   const int L = p - 1;
   if (d == o.c) return false;
@@ -805,7 +810,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
     // fail a positive condition here, and most induced non-arcs are settled
     uint64_t settled = 0;
     for (int j = 0; j < nc; ++j) {
-      if (j == drive) continue;
+      if (j == drive || j == first) continue;
       const Cons cs = P.cons[p][j];
       const bool mine = cs.q == L;
       const int32_t fq = mine ? o.c : S.map[cs.q];
@@ -1002,6 +1007,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
   const bool mine = (m >> lane) & 1u;
   LeafOwner o{};
   int32_t drv_j = 0, drv_lo = 0, drv_len = 0, drv_kind = 0;
+  int4 probe = make_int4(0, 0, 0, 0);
   if (mine) {
     const int32_t c = __ldg(adj + base + lane);
     const int4 vi = __ldg(&G.vi[c]);
@@ -1051,6 +1057,17 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
       }
     }
     drv_len = best;
+    // the first other positive condition: one filter probe per candidate
+    // rejects most of them before the general check runs
+    for (int j = 0; j < npos; ++j) {
+      if (j == drv_j) continue;
+      const Cons cs = P.cons[p][j];
+      const bool own = cs.q == L;
+      const int32_t rlen = own ? (cs.kind == kOut ? o.own[0].y : o.own[1].y) : grp[P.gbase[p] + j].y;
+      if (use_filter(G, rlen))
+        probe = make_int4(own ? c : S.map[cs.q], 1 | (cs.kind == kOut ? 2 : 0) | (j << 8), cs.lab, rlen);
+      break;
+    }
   }
   const uint32_t keep = __ballot_sync(kFull, mine && drv_len > kFlatMax);
   const int32_t len = (mine && drv_len <= kFlatMax) ? drv_len : 0;
@@ -1064,6 +1081,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
   const int32_t total = __shfl_sync(kFull, incl, 31);
   S.owners[lane] = o;  // lanes without a survivor own an empty range
   S.owner_drive[lane] = make_int4(drv_j, drv_lo, drv_kind, excl);
+  S.owner_probe[lane] = probe;
   __syncwarp();
   if (kC && lane == 0 && total) {
     atomicAdd(&ctl->level_chunks[p], (unsigned long long)((total + 31) / 32));
@@ -1104,7 +1122,18 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     }
     const LeafOwner &oo = S.owners[ow];
     bool ok = false;
-    if (g < total) ok = check_leaf<kC, kSym>(G, P, S, grp, p, S.owner_drive[ow].x, d, oo, root_mask, ctr);
+    if (g < total) {
+      const int4 pr = S.owner_probe[ow];
+      ok = true;
+      if (pr.y & 1) {
+        const bool fwd = pr.y & 2;
+        if (kC) ctr.model += search_bytes(pr.w);
+        ok = arc_maybe_l<kC>(G, fwd ? pr.x : d, fwd ? d : pr.x, pr.z, ctr);
+      }
+      if (ok)
+        ok = check_leaf<kC, kSym>(G, P, S, grp, p, S.owner_drive[ow].x, (pr.y & 1) ? (pr.y >> 8) : -1, d,
+                                  oo, root_mask, ctr);
+    }
     if (kShared) {
       expand_position1<kRows, kC>(G, P, S, A, ok, L, oo.c, d, lane, task_count, S.row_cursor, S.row_base,
                                   S.row_cap, ctr);

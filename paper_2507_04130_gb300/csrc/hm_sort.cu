@@ -41,24 +41,51 @@ struct KeySpec {
   int bits[kMaxKeyCols];     // significant bits of each key column (1..32)
   uint32_t xr[kMaxKeyCols];  // xor applied to a column before its bits are taken
   int shift;                 // bit position of this pass's digit within the whole key
+  // the pass's digit as pieces of the columns it overlaps (set by set_pass):
+  // digit |= ((word[tcol[t]] ^ txr[t]) >> tshr[t] & tmask[t]) << tshl[t]
+  int nterm;
+  int tcol[kMaxKeyCols], tshr[kMaxKeyCols], tshl[kMaxKeyCols];
+  uint32_t tmask[kMaxKeyCols], txr[kMaxKeyCols];
 };
 
-// kDigitBits-bit digit starting at bit `shift` of the concatenated key of a row.
-__device__ __forceinline__ uint32_t digit_of(const int32_t *__restrict__ row, const KeySpec &ks) {
-  uint32_t v = 0;
-  int got = 0;
-  int col_lo = 0;  // bit position of the current column's least significant bit
+// The pieces of the kDigitBits-bit digit starting at bit `shift` of the
+// concatenated key (least significant column last in cols[]).
+void set_pass(KeySpec &ks, int shift) {
+  ks.shift = shift;
+  ks.nterm = 0;
+  int got = 0, col_lo = 0;
   for (int i = ks.ncols - 1; i >= 0 && got < kDigitBits; --i) {
     const int b = ks.bits[i];
-    const int want_lo = ks.shift + got;
+    const int want_lo = shift + got;
     if (want_lo < col_lo + b) {
       const int r = want_lo - col_lo;
-      const int take = min(b - r, kDigitBits - got);
-      const uint32_t col = (uint32_t)__ldg(row + ks.cols[i]) ^ ks.xr[i];
-      v |= ((col >> r) & ((take >= 32) ? 0xffffffffu : ((1u << take) - 1u))) << got;
+      const int take = std::min(b - r, kDigitBits - got);
+      const int t = ks.nterm++;
+      ks.tcol[t] = ks.cols[i];
+      ks.tshr[t] = r;
+      ks.tmask[t] = take >= 32 ? 0xffffffffu : ((1u << take) - 1u);
+      ks.tshl[t] = got;
+      ks.txr[t] = ks.xr[i];
       got += take;
     }
     col_lo += b;
+  }
+}
+
+__device__ __forceinline__ uint32_t digit_of(const int32_t *__restrict__ row, const KeySpec &ks) {
+  uint32_t v = 0;
+  for (int t = 0; t < ks.nterm; ++t)
+    v |= ((((uint32_t)__ldg(row + ks.tcol[t]) ^ ks.txr[t]) >> ks.tshr[t]) & ks.tmask[t]) << ks.tshl[t];
+  return v;
+}
+
+// The same digit of a four-word row already in registers.
+__device__ __forceinline__ uint32_t digit_of4(int4 r, const KeySpec &ks) {
+  uint32_t v = 0;
+  for (int t = 0; t < ks.nterm; ++t) {
+    const int c = ks.tcol[t];
+    const uint32_t col = (uint32_t)(c == 0 ? r.x : c == 1 ? r.y : c == 2 ? r.z : r.w) ^ ks.txr[t];
+    v |= ((col >> ks.tshr[t]) & ks.tmask[t]) << ks.tshl[t];
   }
   return v;
 }
@@ -73,6 +100,20 @@ k_hist(const int32_t *__restrict__ rows, int64_t nrows, int width, int64_t per_b
   int64_t hi = min(nrows, lo + per_block);
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
     atomicAdd(&h[digit_of(rows + i * width, ks)], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * grid + blockIdx.x] = h[d];
+}
+
+// The same histogram over four-word rows read as int4 (16-byte aligned rows).
+__global__ void __launch_bounds__(kSortThreads)
+k_hist4(const int4 *__restrict__ rows, int64_t nrows, int64_t per_block, KeySpec ks,
+        uint32_t *__restrict__ hist, int grid) {
+  __shared__ uint32_t h[kRadix];
+  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  int64_t lo = (int64_t)blockIdx.x * per_block;
+  int64_t hi = min(nrows, lo + per_block);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[digit_of4(__ldg(rows + i), ks)], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * grid + blockIdx.x] = h[d];
 }
@@ -181,34 +222,12 @@ k_scatter(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nro
 // matches of 4-vertex patterns), with coalesced writes: each row is loaded
 // once as an int4, the tile is reordered by digit in shared memory, and the
 // tile's run of each digit is written out by consecutive threads.
-__device__ __forceinline__ uint32_t digit_of4(int4 r, const KeySpec &ks) {
-  const int32_t w[4] = {r.x, r.y, r.z, r.w};
-  uint32_t v = 0;
-  int got = 0;
-  int col_lo = 0;
-#pragma unroll
-  for (int i = kMaxKeyCols - 1; i >= 0; --i) {
-    if (i >= ks.ncols || got >= kDigitBits) continue;
-    const int b = ks.bits[i];
-    const int want_lo = ks.shift + got;
-    if (want_lo < col_lo + b) {
-      const int r0 = want_lo - col_lo;
-      const int take = min(b - r0, kDigitBits - got);
-      const int c = ks.cols[i];
-      const uint32_t col = (uint32_t)(c == 0 ? w[0] : c == 1 ? w[1] : c == 2 ? w[2] : w[3]) ^ ks.xr[i];
-      v |= ((col >> r0) & ((take >= 32) ? 0xffffffffu : ((1u << take) - 1u))) << got;
-      got += take;
-    }
-    col_lo += b;
-  }
-  return v;
-}
 
 __global__ void __launch_bounds__(kSortThreads)
 k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, int64_t per_block, KeySpec ks,
            const uint32_t *__restrict__ starts, int grid) {
   __shared__ uint32_t s_base[kRadix];                  // global start of each digit for this block
-  __shared__ uint16_t s_cnt[kSortWarps][kRadix];       // per-warp digit counts, then warp offsets
+  __shared__ __align__(16) uint16_t s_cnt[kSortWarps][kRadix];  // per-warp digit counts, then warp offsets
   __shared__ uint16_t s_first[kRadix];                 // tile-local start of each digit
   __shared__ uint16_t s_num[kRadix];                   // tile count of each digit
   __shared__ int4 s_rows[kTile];                       // the tile in digit order
@@ -220,17 +239,30 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
   const int64_t lo = (int64_t)blockIdx.x * per_block;
   const int64_t hi = min(nrows, lo + per_block);
   const uint32_t lt = lanemask_lt();
+  // each tile's rows are loaded while the previous tile is being reordered
+  int4 next[kItems];
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t i = lo + warp * 32 * kItems + r * 32 + lane;
+    next[r] = i < hi ? in[i] : make_int4(0, 0, 0, 0);
+  }
   for (int64_t tile = lo; tile < hi; tile += kTile) {
     const int tn = (int)min((int64_t)kTile, hi - tile);
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
-    __syncthreads();
+    for (int i = threadIdx.x; i < kSortWarps * kRadix / 8; i += blockDim.x)
+      reinterpret_cast<uint4 *>(&s_cnt[0][0])[i] = make_uint4(0, 0, 0, 0);
     int4 row[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      row[r] = next[r];
+      const int64_t i = tile + kTile + warp * 32 * kItems + r * 32 + lane;
+      next[r] = i < hi ? in[i] : make_int4(0, 0, 0, 0);
+    }
+    __syncthreads();
     uint32_t dig[kItems], rank[kItems];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       const int li = warp * 32 * kItems + r * 32 + lane;
       const bool valid = li < tn;
-      row[r] = valid ? in[tile + li] : make_int4(0, 0, 0, 0);
       const uint32_t d = valid ? digit_of4(row[r], ks) : kRadix;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const int leader = __ffs(peers) - 1;
@@ -599,8 +631,12 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
   uint32_t *starts = hist + nhist, *sums = starts + nhist;
   int32_t *a = rows, *b = tmp;
   for (int p = 0; p < passes; ++p) {
-    ks.shift = p * kDigitBits;
-    k_hist<<<grid, kSortThreads, 0, stream>>>(a, nrows, width, per_block, ks, hist, grid);
+    set_pass(ks, p * kDigitBits);
+    if (width == 4 && ((reinterpret_cast<uintptr_t>(a) & 15u) == 0))
+      k_hist4<<<grid, kSortThreads, 0, stream>>>(reinterpret_cast<const int4 *>(a), nrows, per_block, ks, hist,
+                                                 grid);
+    else
+      k_hist<<<grid, kSortThreads, 0, stream>>>(a, nrows, width, per_block, ks, hist, grid);
     // exclusive scan of the (digit, block) counts over many blocks
     k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, stream>>>(hist, nhist, sums);
     k_scan<<<1, 1024, 0, stream>>>(sums, tiles);
