@@ -459,13 +459,13 @@ hm_status run_batch(const hm_graph *g, const hm_pattern *const *pats, const int3
     bits[c] = c == 0 ? bits_for(npat) : bits_for(g->n);
     xr[c] = 0;
   }
-  hm_status r = radix_sort_rows_cols(packed, tmp, (int64_t)total, width, cols, bits, xr, width, s);
+  int nl = 0;
+  hm_status r = radix_sort_rows_cols(packed, tmp, (int64_t)total, width, cols, bits, xr, width, s, &nl);
   if (r != HM_OK) return r;
   k_unpack_rows<<<grid_r, 256, 0, s>>>(packed, d_off, d_start, d_ks, total, width, rows);
   t_sort.stop();
   HM_CUDA_TRY(cudaGetLastError());
-  int total_bits = bits_for(npat) + kmax * bits_for(g->n);
-  st.kernel_launches += 2 + radix_sort_launches(total_bits);
+  st.kernel_launches += 2 + nl;
   if (timing) {
     HM_CUDA_TRY(cudaStreamSynchronize(s));
     st.ms_sort = t_sort.ms();

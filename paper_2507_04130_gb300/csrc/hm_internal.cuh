@@ -396,17 +396,16 @@ uint64_t budget_chunks();
 // listed in key_cols (most significant first); every key value must lie in
 // [0, 2^bits).  `rows` and `tmp` hold nrows*width words each; the sorted rows
 // end in `rows`.  Stable.  Launches on `stream`.
+// *launches (if given) receives the number of kernels it launched.
 hm_status radix_sort_rows(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
-                          const int *key_cols, int nkey, int bits, cudaStream_t stream);
+                          const int *key_cols, int nkey, int bits, cudaStream_t stream,
+                          int *launches = nullptr);
 
 // As radix_sort_rows, with a bit width (1..32) and an xor mask per key column
 // (the xor maps signed values to an unsigned order, e.g. 0x80000000).
 hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
                                const int *key_cols, const int *key_bits, const uint32_t *key_xor,
-                               int nkey, cudaStream_t stream);
-
-// Kernel launches of one radix_sort_rows_cols call over keys of total_bits bits.
-int radix_sort_launches(int total_bits);
+                               int nkey, cudaStream_t stream, int *launches = nullptr);
 
 // out[i] = in[0] + ... + in[i-1] for i in [0, n); values and total below 2^32.
 hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t stream);

@@ -181,10 +181,11 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     if (ns > 0) {
       const int cols[2] = {0, 1};
       int2 *sd = const_cast<int2 *>(seeds);
+      int nl = 0;
       hm_status r = radix_sort_rows(reinterpret_cast<int32_t *>(sd), tmp, (int64_t)ns, 2, cols, 2,
-                                    bits_for(g->n), s);
+                                    bits_for(g->n), s, &nl);
       if (r != HM_OK) return r;
-      launches += radix_sort_launches(2 * bits_for(g->n));
+      launches += nl;
       const int gb = (int)std::min<unsigned long long>((ns + 256) / 256, (unsigned long long)sms * 8);
       k_seed_group_flags<<<gb, 256, 0, s>>>(seeds, (int64_t)ns, plan.induced ? kInducedGroupCap : 0, flag);
       r = exclusive_scan_u32(flag, idx, (int64_t)ns + 1, s);
@@ -286,8 +287,9 @@ hm_status run_match(const hm_graph *g, const hm_pattern *p, hm_mode mode, int32_
     int cols[kMaxK];
     for (int i = 0; i < p->k; ++i) cols[i] = i;
     const int sort_cols = p->k;
-    hm_status r = radix_sort_rows(out, tmp, (int64_t)h.count, p->k, cols, sort_cols, bits_for(g->n), s);
-    st.kernel_launches += radix_sort_launches(sort_cols * bits_for(g->n));
+    int nl = 0;
+    hm_status r = radix_sort_rows(out, tmp, (int64_t)h.count, p->k, cols, sort_cols, bits_for(g->n), s, &nl);
+    st.kernel_launches += nl;
     t.stop();
     if (r != HM_OK) return r;
     if (timing) {

@@ -8,16 +8,20 @@
 // consumed kDigitBits (10) bits per pass, so a 4-column key of 20-bit vertex
 // ids takes 8 passes.
 //
-// One pass = three kernels on a fixed grid of G blocks, block b owning the
-// contiguous row range [b*R, (b+1)*R):
-//   k_hist     per-block digit histogram          -> hist[digit * G + b]
-//   k_scan     exclusive scan of hist (one block)  -> global start of each
+// One pass on a fixed grid of G blocks, block b owning the contiguous row
+// range [b*R, (b+1)*R):
+//   histogram  per-block digit counts               -> hist[digit * G + b]
+//   scan       exclusive scan of hist               -> global start of each
 //              (digit, block) bucket
-//   k_scatter  the block walks its range in tiles of 1024 rows; inside a
+//   scatter    the block walks its range in tiles of 1024 rows; inside a
 //              tile each warp ranks its 4 rounds of 32 rows with
 //              __match_any_sync, warps are ordered by an exclusive prefix over
 //              their per-digit counts, so equal digits keep input order
-//              (stability), and rows are copied to their final slots.
+//              (stability), the tile is reordered by digit in shared memory
+//              and each digit's run is written by consecutive threads.
+// Rows of four words (16-byte aligned) run every pass in one cooperative
+// launch (k_sort4_fused: the phases separated by grid-wide barriers); other
+// widths run each pass as five kernels (k_hist, three scan kernels, scatter).
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
@@ -83,6 +87,25 @@ __device__ __forceinline__ uint32_t digit_of(const int32_t *__restrict__ row, co
 __device__ __forceinline__ uint32_t digit_of4(int4 r, const KeySpec &ks) {
   uint32_t v = 0;
   for (int t = 0; t < ks.nterm; ++t) {
+    const int c = ks.tcol[t];
+    const uint32_t col = (uint32_t)(c == 0 ? r.x : c == 1 ? r.y : c == 2 ? r.z : r.w) ^ ks.txr[t];
+    v |= ((col >> ks.tshr[t]) & ks.tmask[t]) << ks.tshl[t];
+  }
+  return v;
+}
+
+// A pass's digit over four-word rows: at most four column pieces.
+struct Digit4 {
+  int nterm;
+  int tcol[4], tshr[4], tshl[4];
+  uint32_t tmask[4], txr[4];
+};
+
+__device__ __forceinline__ uint32_t digit_of4(int4 r, const Digit4 &ks) {
+  uint32_t v = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (t >= ks.nterm) break;
     const int c = ks.tcol[t];
     const uint32_t col = (uint32_t)(c == 0 ? r.x : c == 1 ? r.y : c == 2 ? r.z : r.w) ^ ks.txr[t];
     v |= ((col >> ks.tshr[t]) & ks.tmask[t]) << ks.tshl[t];
@@ -223,39 +246,41 @@ k_scatter(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nro
 // once as an int4, the tile is reordered by digit in shared memory, and the
 // tile's run of each digit is written out by consecutive threads.
 
-__global__ void __launch_bounds__(kSortThreads)
-k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, int64_t per_block, KeySpec ks,
-           const uint32_t *__restrict__ starts, int grid) {
-  __shared__ uint32_t s_base[kRadix];                  // global start of each digit for this block
-  __shared__ __align__(16) uint16_t s_cnt[kSortWarps][kRadix];  // per-warp digit counts, then warp offsets
-  __shared__ uint16_t s_first[kRadix];                 // tile-local start of each digit
-  __shared__ uint16_t s_num[kRadix];                   // tile count of each digit
-  __shared__ int4 s_rows[kTile];                       // the tile in digit order
-  __shared__ uint16_t s_dig[kTile];                    // digit of each reordered row
-  __shared__ uint32_t s_wsum[kSortWarps];
+// Shared memory of one block's reorder-then-write pass over four-word rows.
+struct Scatter4Smem {
+  uint32_t base[kRadix];                   // global start of each digit for this block
+  __align__(16) uint16_t cnt[kSortWarps][kRadix];  // per-warp digit counts, then warp offsets
+  uint16_t first[kRadix];                  // tile-local start of each digit
+  uint16_t num[kRadix];                    // tile count of each digit
+  int4 rows[kTile];                        // the tile in digit order
+  uint16_t dig[kTile];                     // digit of each reordered row
+  uint32_t wsum[kSortWarps];
+};
+
+// Rows [lo, hi) of `in` to their places in `out`; sm.base holds the block's
+// global start of each digit (written before the call by the whole block).
+template <class Spec>
+__device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t lo,
+                                               int64_t hi, const Spec &ks, Scatter4Smem &sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-    s_base[d] = starts[(int64_t)d * grid + blockIdx.x];
-  const int64_t lo = (int64_t)blockIdx.x * per_block;
-  const int64_t hi = min(nrows, lo + per_block);
   const uint32_t lt = lanemask_lt();
   // each tile's rows are loaded while the previous tile is being reordered
   int4 next[kItems];
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t i = lo + warp * 32 * kItems + r * 32 + lane;
-    next[r] = i < hi ? in[i] : make_int4(0, 0, 0, 0);
+    next[r] = i < hi ? __ldcg(in + i) : make_int4(0, 0, 0, 0);
   }
   for (int64_t tile = lo; tile < hi; tile += kTile) {
     const int tn = (int)min((int64_t)kTile, hi - tile);
     for (int i = threadIdx.x; i < kSortWarps * kRadix / 8; i += blockDim.x)
-      reinterpret_cast<uint4 *>(&s_cnt[0][0])[i] = make_uint4(0, 0, 0, 0);
+      reinterpret_cast<uint4 *>(&sm.cnt[0][0])[i] = make_uint4(0, 0, 0, 0);
     int4 row[kItems];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       row[r] = next[r];
       const int64_t i = tile + kTile + warp * 32 * kItems + r * 32 + lane;
-      next[r] = i < hi ? in[i] : make_int4(0, 0, 0, 0);
+      next[r] = i < hi ? __ldcg(in + i) : make_int4(0, 0, 0, 0);
     }
     __syncthreads();
     uint32_t dig[kItems], rank[kItems];
@@ -268,8 +293,8 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
       const int leader = __ffs(peers) - 1;
       uint32_t prev = 0;
       if (valid && lane == leader) {
-        prev = s_cnt[warp][d];
-        s_cnt[warp][d] = (uint16_t)(prev + __popc(peers));
+        prev = sm.cnt[warp][d];
+        sm.cnt[warp][d] = (uint16_t)(prev + __popc(peers));
       }
       prev = __shfl_sync(0xffffffffu, prev, leader);
       dig[r] = d;
@@ -282,11 +307,11 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
       uint32_t acc = 0;
 #pragma unroll
       for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t t = s_cnt[w][d];
-        s_cnt[w][d] = (uint16_t)acc;
+        const uint32_t t = sm.cnt[w][d];
+        sm.cnt[w][d] = (uint16_t)acc;
         acc += t;
       }
-      s_num[d] = (uint16_t)acc;
+      sm.num[d] = (uint16_t)acc;
     }
     __syncthreads();
     // tile-local start of each digit: exclusive scan of s_num (kRadix / kSortThreads per thread)
@@ -295,7 +320,7 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
       uint32_t v[kPer], sum = 0;
 #pragma unroll
       for (int t = 0; t < kPer; ++t) {
-        v[t] = s_num[threadIdx.x * kPer + t];
+        v[t] = sm.num[threadIdx.x * kPer + t];
         sum += v[t];
       }
       uint32_t x = sum;
@@ -304,13 +329,13 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      if (lane == 31) s_wsum[warp] = x;
+      if (lane == 31) sm.wsum[warp] = x;
       __syncthreads();
       uint32_t before = x - sum;
-      for (int w = 0; w < warp; ++w) before += s_wsum[w];
+      for (int w = 0; w < warp; ++w) before += sm.wsum[w];
 #pragma unroll
       for (int t = 0; t < kPer; ++t) {
-        s_first[threadIdx.x * kPer + t] = (uint16_t)before;
+        sm.first[threadIdx.x * kPer + t] = (uint16_t)before;
         before += v[t];
       }
     }
@@ -321,21 +346,31 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
       const int li = warp * 32 * kItems + r * 32 + lane;
       if (li < tn) {
         const uint32_t d = dig[r];
-        const int lp = s_first[d] + s_cnt[warp][d] + rank[r];
-        s_rows[lp] = row[r];
-        s_dig[lp] = (uint16_t)d;
+        const int lp = sm.first[d] + sm.cnt[warp][d] + rank[r];
+        sm.rows[lp] = row[r];
+        sm.dig[lp] = (uint16_t)d;
       }
     }
     __syncthreads();
     // consecutive threads write consecutive rows of each digit's run
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
-      const uint32_t d = s_dig[t];
-      out[(int64_t)s_base[d] + (t - s_first[d])] = s_rows[t];
+      const uint32_t d = sm.dig[t];
+      out[(int64_t)sm.base[d] + (t - sm.first[d])] = sm.rows[t];
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) s_base[d] += s_num[d];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sm.base[d] += sm.num[d];
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, int64_t per_block, KeySpec ks,
+           const uint32_t *__restrict__ starts, int grid) {
+  __shared__ Scatter4Smem sm;
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    sm.base[d] = starts[(int64_t)d * grid + blockIdx.x];
+  const int64_t lo = (int64_t)blockIdx.x * per_block;
+  scatter4_range(in, out, lo, min(nrows, lo + per_block), ks, sm);
 }
 
 // The same reorder-then-write pass for rows of W words (2..8), staged as
@@ -519,6 +554,117 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
   return before;
 }
 
+// ---- all passes in one cooperative launch (four-word rows) ------------------
+//
+// Every block of the grid is resident (cooperative launch), so the three
+// phases of a pass -- per-block histogram, per-digit prefix over blocks,
+// reorder-then-write -- are separated by grid-wide barriers instead of
+// kernel boundaries.  Data that other blocks wrote is read through L2
+// (__ldcg).  A barrier waits at most kBarrierNs (long enough for blocks that
+// wait for SMs held by kernels of other streams); a block that gives up sets
+// *err and returns, and every other block returns at its next barrier, so
+// the launch always ends (the host then reports an error).
+constexpr int kMaxSortPasses = (4 * 32 + kDigitBits - 1) / kDigitBits;
+constexpr uint64_t kBarrierNs = 10ull * 1000 * 1000 * 1000;
+
+struct FusedSort4 {
+  int4 *a, *b;                 // pass p reads a (p even) or b and writes the other
+  int64_t nrows, per_block;
+  int grid, passes;
+  uint32_t *hist;              // [kRadix * grid] per-block digit counts
+  uint32_t *part;              // [kRadix * grid] counts of the same digit in earlier blocks
+  uint32_t *tot;               // [kRadix] digit totals
+  unsigned int *bar;           // arrivals (zero at launch)
+  int *err;                    // set when a barrier gave up
+  Digit4 ks[kMaxSortPasses];
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int target, int *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+      if (*(volatile unsigned int *)bar >= target) break;
+      if (globaltimer_ns() - t0 > kBarrierNs) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    if (*(volatile int *)err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort4_fused(const __grid_constant__ FusedSort4 F) {
+  __shared__ Scatter4Smem sm;
+  const int b = blockIdx.x, grid = F.grid;
+  const int64_t lo = (int64_t)b * F.per_block;
+  const int64_t hi = min(F.nrows, lo + F.per_block);
+  unsigned int target = 0;
+  for (int p = 0; p < F.passes; ++p) {
+    const int4 *in = (p & 1) ? F.b : F.a;
+    int4 *out = (p & 1) ? F.a : F.b;
+    const Digit4 &ks = F.ks[p];
+    // 1. this block's digit counts
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sm.base[d] = 0;
+    __syncthreads();
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&sm.base[digit_of4(__ldcg(in + i), ks)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) F.hist[(int64_t)d * grid + b] = sm.base[d];
+    target += grid;
+    if (!grid_barrier(F.bar, target, F.err)) return;
+    // 2. for the digits this block owns: counts in earlier blocks, and the total
+    for (int d = b; d < kRadix; d += grid) {
+      const uint32_t *h = F.hist + (int64_t)d * grid;
+      uint32_t *q = F.part + (int64_t)d * grid;
+      uint32_t run = 0;
+      for (int c0 = 0; c0 < grid; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const uint32_t v = c < grid ? __ldcg(h + c) : 0u;
+        uint32_t chunk;
+        const uint32_t before = block_excl_scan(v, &chunk);
+        if (c < grid) q[c] = run + before;
+        run += chunk;
+      }
+      if (threadIdx.x == 0) F.tot[d] = run;
+    }
+    target += grid;
+    if (!grid_barrier(F.bar, target, F.err)) return;
+    // 3. global start of each digit for this block, then reorder and write
+    {
+      constexpr int kPer = kRadix / kSortThreads;
+      uint32_t v[kPer], sum = 0;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        v[t] = __ldcg(F.tot + threadIdx.x * kPer + t);
+        sum += v[t];
+      }
+      uint32_t all;
+      uint32_t before = block_excl_scan(sum, &all);
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int d = threadIdx.x * kPer + t;
+        sm.base[d] = before + __ldcg(F.part + (int64_t)d * grid + b);
+        before += v[t];
+      }
+    }
+    __syncthreads();
+    scatter4_range(in, out, lo, hi, ks, sm);
+    if (p + 1 == F.passes) break;
+    target += grid;
+    if (!grid_barrier(F.bar, target, F.err)) return;
+  }
+}
+
 __global__ void __launch_bounds__(kScanThreads)
 k_tile_sums(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ sums) {
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
@@ -567,9 +713,6 @@ hm_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaS
 }
 
 
-int radix_sort_launches(int total_bits) {
-  return 5 * ((total_bits + kDigitBits - 1) / kDigitBits);  // hist, 3 scan kernels, scatter per pass
-}
 
 int bits_for(int64_t n) {
   int b = 1;
@@ -591,7 +734,7 @@ int num_sms() {
 }
 
 hm_status radix_sort_rows(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
-                          const int *key_cols, int nkey, int bits, cudaStream_t stream) {
+                          const int *key_cols, int nkey, int bits, cudaStream_t stream, int *launches) {
   int b[kMaxKeyCols];
   uint32_t x[kMaxKeyCols];
   if (nkey < 1 || nkey > kMaxKeyCols) return HM_ERR_ARG;
@@ -599,12 +742,81 @@ hm_status radix_sort_rows(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
     b[i] = bits;
     x[i] = 0;
   }
-  return radix_sort_rows_cols(rows, tmp, nrows, width, key_cols, b, x, nkey, stream);
+  return radix_sort_rows_cols(rows, tmp, nrows, width, key_cols, b, x, nkey, stream, launches);
+}
+
+// All passes of a sort of 16-byte aligned four-word rows in one cooperative
+// launch.  *ran is false (and nothing was launched) when the device cannot
+// hold a grid of resident blocks for it; the caller then runs the passes as
+// separate kernels.
+static hm_status sort4_fused(int32_t *rows, int32_t *tmp, int64_t nrows, KeySpec ks, int passes,
+                             cudaStream_t stream, bool *ran) {
+  *ran = false;
+  static std::atomic<int> per_sm{-1};
+  int nb = per_sm.load(std::memory_order_relaxed);
+  if (nb < 0) {
+    int coop = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sort4_fused, kSortThreads, 0) != cudaSuccess)
+      nb = 0;
+    cudaGetLastError();
+    per_sm.store(nb, std::memory_order_relaxed);
+  }
+  if (nb <= 0 || passes > kMaxSortPasses) return HM_OK;
+  int grid = (int)std::min<int64_t>((nrows + kTile - 1) / kTile, (int64_t)num_sms() * nb);
+  int64_t per_block = (nrows + grid - 1) / grid;
+  per_block = (per_block + kTile - 1) / kTile * kTile;
+  grid = (int)((nrows + per_block - 1) / per_block);
+  const int64_t nhist = (int64_t)kRadix * grid;
+  uint32_t *buf = nullptr;
+  HM_CUDA_TRY(cudaMallocAsync(&buf, sizeof(uint32_t) * (size_t)(2 * nhist + kRadix + 4), stream));
+  FusedSort4 F{};
+  F.a = reinterpret_cast<int4 *>(rows);
+  F.b = reinterpret_cast<int4 *>(tmp);
+  F.nrows = nrows;
+  F.per_block = per_block;
+  F.grid = grid;
+  F.passes = passes;
+  F.hist = buf;
+  F.part = buf + nhist;
+  F.tot = buf + 2 * nhist;
+  F.bar = reinterpret_cast<unsigned int *>(buf + 2 * nhist + kRadix);
+  F.err = reinterpret_cast<int *>(buf + 2 * nhist + kRadix + 1);
+  for (int p = 0; p < passes; ++p) {
+    set_pass(ks, p * kDigitBits);
+    Digit4 &d = F.ks[p];
+    d.nterm = ks.nterm;
+    for (int t = 0; t < ks.nterm; ++t) {
+      d.tcol[t] = ks.tcol[t];
+      d.tshr[t] = ks.tshr[t];
+      d.tshl[t] = ks.tshl[t];
+      d.tmask[t] = ks.tmask[t];
+      d.txr[t] = ks.txr[t];
+    }
+  }
+  HM_CUDA_TRY(cudaMemsetAsync(F.bar, 0, 2 * sizeof(uint32_t), stream));
+  void *args[] = {&F};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_sort4_fused, dim3(grid), dim3(kSortThreads),
+                                                    args, 0, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not launched: the caller takes the multi-kernel path
+    HM_CUDA_TRY(cudaFreeAsync(buf, stream));
+    return HM_OK;
+  }
+  *ran = true;
+  if (passes & 1)
+    HM_CUDA_TRY(cudaMemcpyAsync(rows, tmp, sizeof(int4) * (size_t)nrows, cudaMemcpyDeviceToDevice, stream));
+  int err = 0;
+  HM_CUDA_TRY(cudaMemcpyAsync(&err, F.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  HM_CUDA_TRY(cudaFreeAsync(buf, stream));
+  HM_CUDA_TRY(cudaStreamSynchronize(stream));
+  return err ? HM_ERR_CUDA : HM_OK;
 }
 
 hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int width,
                                const int *key_cols, const int *key_bits, const uint32_t *key_xor,
-                               int nkey, cudaStream_t stream) {
+                               int nkey, cudaStream_t stream, int *launches) {
   if (nrows <= 1) return HM_OK;
   ScatterFn scatter = scatter_for(width);
   if (!scatter || nkey < 1 || nkey > kMaxKeyCols) return HM_ERR_ARG;
@@ -620,6 +832,16 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
     total_bits += key_bits[i];
   }
   const int passes = (total_bits + kDigitBits - 1) / kDigitBits;
+  if (launches) *launches = 5 * passes;
+  if (width == 4 && (((reinterpret_cast<uintptr_t>(rows) | reinterpret_cast<uintptr_t>(tmp)) & 15u) == 0)) {
+    bool ran = false;
+    const hm_status fs = sort4_fused(rows, tmp, nrows, ks, passes, stream, &ran);
+    if (fs != HM_OK) return fs;
+    if (ran) {
+      if (launches) *launches = 1;
+      return HM_OK;
+    }
+  }
   int grid = (int)std::min<int64_t>((nrows + kTile - 1) / kTile, (int64_t)num_sms() * 4);
   int64_t per_block = (nrows + grid - 1) / grid;
   per_block = (per_block + kTile - 1) / kTile * kTile;
