@@ -250,8 +250,8 @@ k_scatter(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nro
 struct Scatter4Smem {
   uint32_t base[kRadix];                   // global start of each digit for this block
   __align__(16) uint16_t cnt[kSortWarps][kRadix];  // per-warp digit counts, then warp offsets
-  uint16_t first[kRadix];                  // tile-local start of each digit
-  uint16_t num[kRadix];                    // tile count of each digit
+  __align__(8) uint16_t first[kRadix];     // tile-local start of each digit
+  __align__(8) uint16_t num[kRadix];       // tile count of each digit
   int4 rows[kTile];                        // the tile in digit order
   uint16_t dig[kTile];                     // digit of each reordered row
   uint32_t wsum[kSortWarps];
@@ -302,27 +302,25 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
       __syncwarp();
     }
     __syncthreads();
-    // per digit: warp offsets (in place) and the tile count
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-      uint32_t acc = 0;
+    // per digit: warp offsets (in place), the tile count and the tile-local
+    // start; each thread owns four consecutive digits, whose 16-bit counters
+    // it moves as one 64-bit word (a tile holds at most 1024 rows, so no
+    // 16-bit lane of a sum carries into the next)
+    {
+      static_assert(kRadix == 4 * kSortThreads, "four digits per thread");
+      const int d0 = threadIdx.x * 4;
+      uint64_t acc = 0;
 #pragma unroll
       for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t t = sm.cnt[w][d];
-        sm.cnt[w][d] = (uint16_t)acc;
+        uint64_t *c = reinterpret_cast<uint64_t *>(&sm.cnt[w][d0]);
+        const uint64_t t = *c;
+        *c = acc;
         acc += t;
       }
-      sm.num[d] = (uint16_t)acc;
-    }
-    __syncthreads();
-    // tile-local start of each digit: exclusive scan of s_num (kRadix / kSortThreads per thread)
-    {
-      constexpr int kPer = kRadix / kSortThreads;
-      uint32_t v[kPer], sum = 0;
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        v[t] = sm.num[threadIdx.x * kPer + t];
-        sum += v[t];
-      }
+      *reinterpret_cast<uint64_t *>(&sm.num[d0]) = acc;
+      const uint32_t v0 = (uint32_t)(acc & 0xffff), v1 = (uint32_t)((acc >> 16) & 0xffff),
+                     v2 = (uint32_t)((acc >> 32) & 0xffff);
+      const uint32_t sum = v0 + v1 + v2 + (uint32_t)(acc >> 48);
       uint32_t x = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -333,11 +331,8 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
       __syncthreads();
       uint32_t before = x - sum;
       for (int w = 0; w < warp; ++w) before += sm.wsum[w];
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        sm.first[threadIdx.x * kPer + t] = (uint16_t)before;
-        before += v[t];
-      }
+      const uint64_t f0 = before, f1 = before + v0, f2 = f1 + v1, f3 = f2 + v2;
+      *reinterpret_cast<uint64_t *>(&sm.first[d0]) = f0 | (f1 << 16) | (f2 << 32) | (f3 << 48);
     }
     __syncthreads();
     // reorder the tile by digit in shared memory
