@@ -561,6 +561,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 // the launch always ends (the host then reports an error).
 constexpr int kMaxSortPasses = (4 * 32 + kDigitBits - 1) / kDigitBits;
 constexpr uint64_t kBarrierNs = 10ull * 1000 * 1000 * 1000;
+constexpr int kWarpScanBelow = 128;  // grids smaller than this scan one digit per warp
 
 struct FusedSort4 {
   int4 *a, *b;                 // pass p reads a (p even) or b and writes the other
@@ -617,20 +618,45 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort4_fused(const __grid_co
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) F.hist[(int64_t)d * grid + b] = sm.base[d];
     target += grid;
     if (!grid_barrier(F.bar, target, F.err)) return;
-    // 2. for the digits this block owns: counts in earlier blocks, and the total
-    for (int d = b; d < kRadix; d += grid) {
-      const uint32_t *h = F.hist + (int64_t)d * grid;
-      uint32_t *q = F.part + (int64_t)d * grid;
-      uint32_t run = 0;
-      for (int c0 = 0; c0 < grid; c0 += blockDim.x) {
-        const int c = c0 + threadIdx.x;
-        const uint32_t v = c < grid ? __ldcg(h + c) : 0u;
-        uint32_t chunk;
-        const uint32_t before = block_excl_scan(v, &chunk);
-        if (c < grid) q[c] = run + before;
-        run += chunk;
+    // 2. each digit's counts in earlier blocks, and its total: on a large
+    //    grid one block per digit (a block-wide scan per 256 blocks); on a
+    //    small one, where that would leave few blocks scanning many digits
+    //    one after another, one warp per digit
+    if (grid >= kWarpScanBelow) {
+      for (int d = b; d < kRadix; d += grid) {
+        const uint32_t *h = F.hist + (int64_t)d * grid;
+        uint32_t *q = F.part + (int64_t)d * grid;
+        uint32_t run = 0;
+        for (int c0 = 0; c0 < grid; c0 += blockDim.x) {
+          const int c = c0 + threadIdx.x;
+          const uint32_t v = c < grid ? __ldcg(h + c) : 0u;
+          uint32_t chunk;
+          const uint32_t before = block_excl_scan(v, &chunk);
+          if (c < grid) q[c] = run + before;
+          run += chunk;
+        }
+        if (threadIdx.x == 0) F.tot[d] = run;
       }
-      if (threadIdx.x == 0) F.tot[d] = run;
+    } else {
+      const int lane = threadIdx.x & 31, nw = grid * kSortWarps;
+      for (int d = b * kSortWarps + (threadIdx.x >> 5); d < kRadix; d += nw) {
+        const uint32_t *h = F.hist + (int64_t)d * grid;
+        uint32_t *q = F.part + (int64_t)d * grid;
+        uint32_t run = 0;
+        for (int c0 = 0; c0 < grid; c0 += 32) {
+          const int c = c0 + lane;
+          const uint32_t v = c < grid ? __ldcg(h + c) : 0u;
+          uint32_t x = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+          }
+          if (c < grid) q[c] = run + x - v;
+          run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) F.tot[d] = run;
+      }
     }
     target += grid;
     if (!grid_barrier(F.bar, target, F.err)) return;
