@@ -19,9 +19,10 @@
 //              their per-digit counts, so equal digits keep input order
 //              (stability), the tile is reordered by digit in shared memory
 //              and each digit's run is written by consecutive threads.
-// Rows of four words (16-byte aligned) run every pass in one cooperative
-// launch (k_sort4_fused: the phases separated by grid-wide barriers); other
-// widths run each pass as five kernels (k_hist, three scan kernels, scatter).
+// Rows of four words (16-byte aligned, at least kFusedMinRows of them) run
+// every pass in one cooperative launch (k_sort4_fused: the phases separated
+// by grid-wide barriers); other widths and smaller sorts run each pass as
+// five kernels (k_hist, three scan kernels, scatter).
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
@@ -562,6 +563,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 constexpr int kMaxSortPasses = (4 * 32 + kDigitBits - 1) / kDigitBits;
 constexpr uint64_t kBarrierNs = 10ull * 1000 * 1000 * 1000;
 constexpr int kWarpScanBelow = 128;  // grids smaller than this scan one digit per warp
+// The fused sort waits for its barrier status before it returns; below this
+// many rows that wait costs more than the launches it saves, and the sort
+// runs as separate kernels that the caller's next launches can queue behind.
+constexpr int64_t kFusedMinRows = 1 << 18;
 
 struct FusedSort4 {
   int4 *a, *b;                 // pass p reads a (p even) or b and writes the other
@@ -854,7 +859,8 @@ hm_status radix_sort_rows_cols(int32_t *rows, int32_t *tmp, int64_t nrows, int w
   }
   const int passes = (total_bits + kDigitBits - 1) / kDigitBits;
   if (launches) *launches = 5 * passes;
-  if (width == 4 && (((reinterpret_cast<uintptr_t>(rows) | reinterpret_cast<uintptr_t>(tmp)) & 15u) == 0)) {
+  if (width == 4 && nrows >= kFusedMinRows &&
+      (((reinterpret_cast<uintptr_t>(rows) | reinterpret_cast<uintptr_t>(tmp)) & 15u) == 0)) {
     bool ran = false;
     const hm_status fs = sort4_fused(rows, tmp, nrows, ks, passes, stream, &ran);
     if (fs != HM_OK) return fs;
