@@ -64,9 +64,10 @@ def parse_args(argv=None):
                          "ones are added (--profile connectome; default = the full workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="arrival window per rate of the served workload on the primary (connectome-shaped) "
-                         "graph, at most 2,000 queries per rate; a third of it on the R-MAT graph")
+                         "graph, at most 2,000 queries per rate (so each rate serves 2,000 queries or 60 s "
+                         "of arrivals by default); a third of it on the R-MAT graph")
     return ap.parse_args(argv)
 
 

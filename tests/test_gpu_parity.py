@@ -87,9 +87,20 @@ def _export_groups(hm, G):
     return out, nd
 
 
+@pytest.mark.parametrize("big", [False, True], ids=["rmat10", "er400k"])
 @pytest.mark.parametrize("signed_labels", [False, True])
-def test_label_grouped_lists_and_directory(hm, signed_labels):
-    g = synth.config2_graph(scale=10)
+def test_label_grouped_lists_and_directory(hm, signed_labels, big):
+    # er400k: more than 2^18 arcs, so the build's row sorts run as one
+    # cooperative launch, with 13-bit vertex ids and 2-3-bit labels whose
+    # digits span several key columns
+    g = synth.er_graph(6000, 400_000, 3, 5, seed=11) if big else synth.config2_graph(scale=10)
+    if big:
+        ex0 = hm.Graph.from_synth(g).export()
+        o = np.lexsort((g.dst, g.src))
+        np.testing.assert_array_equal(ex0["out_adj"], g.dst[o])
+        np.testing.assert_array_equal(ex0["out_elab"], g.elab[o])
+        i = np.lexsort((g.src, g.dst))
+        np.testing.assert_array_equal(ex0["in_adj"], g.src[i])
     if signed_labels:   # labels outside [0, 2^24) take the 32-bit key path
         g = synth.Graph(g.n, g.src, g.dst, (g.vlab * 1000003 - 5).astype(np.int32),
                         (g.elab * -7).astype(np.int32))
@@ -208,6 +219,30 @@ def test_complete_digraph(hm):
         sp = synth.random_pattern(rng, k, 0.5, n_vlab=1, n_elab=1)
         for mode in MODES:
             _check(hm, G, og, sp, mode)
+
+
+def test_complete_digraph_large_row_sort(hm):
+    """303,600 rows of 5-bit ids: the row sort's single-launch path with digits spanning columns.
+
+    On the complete digraph every injective map is a monomorphism of any
+    4-vertex pattern (the closed form n!/(n-k)!), so the sorted rows are
+    exactly the ordered 4-permutations of 0..24 in lexicographic order.
+    """
+    import itertools
+    n, k = 25, 4
+    G = hm.Graph.from_synth(synth.complete_digraph(n))
+    sp = synth.Pattern(k, np.array([0, 1, 2, 3], np.int32), np.array([1, 2, 3, 0], np.int32),
+                       np.zeros(k, np.int32), np.zeros(k, np.int32))
+    want = np.array(list(itertools.permutations(range(n), k)), np.int32)
+    assert want.shape[0] == 303_600 > (1 << 18)
+    P = hm.Pattern.from_synth(sp)
+    try:
+        hm.set_tuning(symmetry=-1)   # every row found by the search, none as an automorphic image
+        rows = hm.enumerate_matches(G, P, hm.MONO).cpu().numpy()
+    finally:
+        hm.set_tuning()
+    np.testing.assert_array_equal(rows, want)
+    np.testing.assert_array_equal(hm.enumerate_matches(G, P, hm.MONO).cpu().numpy(), want)
 
 
 def test_er_workload_cycle3(hm):
