@@ -128,6 +128,24 @@ k_hist(const int32_t *__restrict__ rows, int64_t nrows, int width, int64_t per_b
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * grid + blockIdx.x] = h[d];
 }
 
+// Digit counts of rows [lo, hi) into h (shared memory), four independent
+// 16-byte loads in flight per thread.
+template <class Spec>
+__device__ __forceinline__ void hist4_range(const int4 *__restrict__ rows, int64_t lo, int64_t hi, const Spec &ks,
+                                            uint32_t *h) {
+  const int64_t step = blockDim.x;
+  int64_t i = lo + threadIdx.x;
+  for (; i + 3 * step < hi; i += 4 * step) {
+    const int4 r0 = __ldcg(rows + i), r1 = __ldcg(rows + i + step), r2 = __ldcg(rows + i + 2 * step),
+               r3 = __ldcg(rows + i + 3 * step);
+    atomicAdd(&h[digit_of4(r0, ks)], 1u);
+    atomicAdd(&h[digit_of4(r1, ks)], 1u);
+    atomicAdd(&h[digit_of4(r2, ks)], 1u);
+    atomicAdd(&h[digit_of4(r3, ks)], 1u);
+  }
+  for (; i < hi; i += step) atomicAdd(&h[digit_of4(__ldcg(rows + i), ks)], 1u);
+}
+
 // The same histogram over four-word rows read as int4 (16-byte aligned rows).
 __global__ void __launch_bounds__(kSortThreads)
 k_hist4(const int4 *__restrict__ rows, int64_t nrows, int64_t per_block, KeySpec ks,
@@ -137,7 +155,7 @@ k_hist4(const int4 *__restrict__ rows, int64_t nrows, int64_t per_block, KeySpec
   __syncthreads();
   int64_t lo = (int64_t)blockIdx.x * per_block;
   int64_t hi = min(nrows, lo + per_block);
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[digit_of4(__ldg(rows + i), ks)], 1u);
+  hist4_range(rows, lo, hi, ks, h);
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * grid + blockIdx.x] = h[d];
 }
@@ -618,7 +636,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort4_fused(const __grid_co
     // 1. this block's digit counts
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sm.base[d] = 0;
     __syncthreads();
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&sm.base[digit_of4(__ldcg(in + i), ks)], 1u);
+    hist4_range(in, lo, hi, ks, sm.base);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) F.hist[(int64_t)d * grid + b] = sm.base[d];
     target += grid;
