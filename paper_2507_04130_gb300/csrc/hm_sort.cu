@@ -128,20 +128,19 @@ k_hist(const int32_t *__restrict__ rows, int64_t nrows, int width, int64_t per_b
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * grid + blockIdx.x] = h[d];
 }
 
-// Digit counts of rows [lo, hi) into h (shared memory), four independent
+// Digit counts of rows [lo, hi) into h (shared memory), eight independent
 // 16-byte loads in flight per thread.
 template <class Spec>
 __device__ __forceinline__ void hist4_range(const int4 *__restrict__ rows, int64_t lo, int64_t hi, const Spec &ks,
                                             uint32_t *h) {
   const int64_t step = blockDim.x;
   int64_t i = lo + threadIdx.x;
-  for (; i + 3 * step < hi; i += 4 * step) {
-    const int4 r0 = __ldcg(rows + i), r1 = __ldcg(rows + i + step), r2 = __ldcg(rows + i + 2 * step),
-               r3 = __ldcg(rows + i + 3 * step);
-    atomicAdd(&h[digit_of4(r0, ks)], 1u);
-    atomicAdd(&h[digit_of4(r1, ks)], 1u);
-    atomicAdd(&h[digit_of4(r2, ks)], 1u);
-    atomicAdd(&h[digit_of4(r3, ks)], 1u);
+  for (; i + 7 * step < hi; i += 8 * step) {
+    int4 r[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) r[t] = __ldcg(rows + i + t * step);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) atomicAdd(&h[digit_of4(r[t], ks)], 1u);
   }
   for (; i < hi; i += step) atomicAdd(&h[digit_of4(__ldcg(rows + i), ks)], 1u);
 }
@@ -267,10 +266,10 @@ k_scatter(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t nro
 
 // Shared memory of one block's reorder-then-write pass over four-word rows.
 struct Scatter4Smem {
-  uint32_t base[kRadix];                   // global start of each digit for this block
+  uint32_t base[2][kRadix];                // global start of each digit for this block's current
+                                           // tile and for the next one (alternating)
   __align__(16) uint16_t cnt[kSortWarps][kRadix];  // per-warp digit counts, then warp offsets
   __align__(8) uint16_t first[kRadix];     // tile-local start of each digit
-  __align__(8) uint16_t num[kRadix];       // tile count of each digit
   int4 rows[kTile];                        // the tile in digit order
   uint16_t dig[kTile];                     // digit of each reordered row
   uint32_t wsum[kSortWarps];
@@ -290,10 +289,12 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
     const int64_t i = lo + warp * 32 * kItems + r * 32 + lane;
     next[r] = i < hi ? __ldcg(in + i) : make_int4(0, 0, 0, 0);
   }
+  for (int i = threadIdx.x; i < kSortWarps * kRadix / 8; i += blockDim.x)
+    reinterpret_cast<uint4 *>(&sm.cnt[0][0])[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  int cur = 0;  // sm.base[cur]: this tile's digit starts (the caller filled sm.base[0])
   for (int64_t tile = lo; tile < hi; tile += kTile) {
     const int tn = (int)min((int64_t)kTile, hi - tile);
-    for (int i = threadIdx.x; i < kSortWarps * kRadix / 8; i += blockDim.x)
-      reinterpret_cast<uint4 *>(&sm.cnt[0][0])[i] = make_uint4(0, 0, 0, 0);
     int4 row[kItems];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
@@ -301,7 +302,6 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
       const int64_t i = tile + kTile + warp * 32 * kItems + r * 32 + lane;
       next[r] = i < hi ? __ldcg(in + i) : make_int4(0, 0, 0, 0);
     }
-    __syncthreads();
     uint32_t dig[kItems], rank[kItems];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
@@ -321,10 +321,10 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
       __syncwarp();
     }
     __syncthreads();
-    // per digit: warp offsets (in place), the tile count and the tile-local
-    // start; each thread owns four consecutive digits, whose 16-bit counters
-    // it moves as one 64-bit word (a tile holds at most 1024 rows, so no
-    // 16-bit lane of a sum carries into the next)
+    // per digit: warp offsets (in place), the tile-local start and the next
+    // tile's global start; each thread owns four consecutive digits, whose
+    // 16-bit counters it moves as one 64-bit word (a tile holds at most 1024
+    // rows, so no 16-bit lane of a sum carries into the next)
     {
       static_assert(kRadix == 4 * kSortThreads, "four digits per thread");
       const int d0 = threadIdx.x * 4;
@@ -336,10 +336,9 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
         *c = acc;
         acc += t;
       }
-      *reinterpret_cast<uint64_t *>(&sm.num[d0]) = acc;
       const uint32_t v0 = (uint32_t)(acc & 0xffff), v1 = (uint32_t)((acc >> 16) & 0xffff),
-                     v2 = (uint32_t)((acc >> 32) & 0xffff);
-      const uint32_t sum = v0 + v1 + v2 + (uint32_t)(acc >> 48);
+                     v2 = (uint32_t)((acc >> 32) & 0xffff), v3 = (uint32_t)(acc >> 48);
+      const uint32_t sum = v0 + v1 + v2 + v3;
       uint32_t x = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -352,6 +351,8 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
       for (int w = 0; w < warp; ++w) before += sm.wsum[w];
       const uint64_t f0 = before, f1 = before + v0, f2 = f1 + v1, f3 = f2 + v2;
       *reinterpret_cast<uint64_t *>(&sm.first[d0]) = f0 | (f1 << 16) | (f2 << 32) | (f3 << 48);
+      const uint4 b = *reinterpret_cast<const uint4 *>(&sm.base[cur][d0]);
+      *reinterpret_cast<uint4 *>(&sm.base[cur ^ 1][d0]) = make_uint4(b.x + v0, b.y + v1, b.z + v2, b.w + v3);
     }
     __syncthreads();
     // reorder the tile by digit in shared memory
@@ -366,14 +367,16 @@ __device__ __forceinline__ void scatter4_range(const int4 *__restrict__ in, int4
       }
     }
     __syncthreads();
-    // consecutive threads write consecutive rows of each digit's run
+    // consecutive threads write consecutive rows of each digit's run; the
+    // counters are cleared for the next tile meanwhile
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
       const uint32_t d = sm.dig[t];
-      out[(int64_t)sm.base[d] + (t - sm.first[d])] = sm.rows[t];
+      out[(int64_t)sm.base[cur][d] + (t - sm.first[d])] = sm.rows[t];
     }
+    for (int i = threadIdx.x; i < kSortWarps * kRadix / 8; i += blockDim.x)
+      reinterpret_cast<uint4 *>(&sm.cnt[0][0])[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sm.base[d] += sm.num[d];
-    __syncthreads();
+    cur ^= 1;
   }
 }
 
@@ -382,7 +385,7 @@ k_scatter4(const int4 *__restrict__ in, int4 *__restrict__ out, int64_t nrows, i
            const uint32_t *__restrict__ starts, int grid) {
   __shared__ Scatter4Smem sm;
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-    sm.base[d] = starts[(int64_t)d * grid + blockIdx.x];
+    sm.base[0][d] = starts[(int64_t)d * grid + blockIdx.x];
   const int64_t lo = (int64_t)blockIdx.x * per_block;
   scatter4_range(in, out, lo, min(nrows, lo + per_block), ks, sm);
 }
@@ -634,11 +637,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort4_fused(const __grid_co
     int4 *out = (p & 1) ? F.a : F.b;
     const Digit4 &ks = F.ks[p];
     // 1. this block's digit counts
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sm.base[d] = 0;
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sm.base[0][d] = 0;
     __syncthreads();
-    hist4_range(in, lo, hi, ks, sm.base);
+    hist4_range(in, lo, hi, ks, sm.base[0]);
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) F.hist[(int64_t)d * grid + b] = sm.base[d];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) F.hist[(int64_t)d * grid + b] = sm.base[0][d];
     target += grid;
     if (!grid_barrier(F.bar, target, F.err)) return;
     // 2. each digit's counts in earlier blocks, and its total: on a large
@@ -697,7 +700,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort4_fused(const __grid_co
 #pragma unroll
       for (int t = 0; t < kPer; ++t) {
         const int d = threadIdx.x * kPer + t;
-        sm.base[d] = before + __ldcg(F.part + (int64_t)d * grid + b);
+        sm.base[0][d] = before + __ldcg(F.part + (int64_t)d * grid + b);
         before += v[t];
       }
     }
