@@ -497,7 +497,10 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic", "config": cfg,
             "latency_ms": {"p50": round(p50, 3), "p99": round(p99, 3), "queries": len(lat),
-                           "per_query": per_query},
+                           "per_query": per_query,
+                           "note": ("the timed calls of three fixed queries, so p99 is the slowest "
+                                    "query's time; latency distributions under load are in "
+                                    "serving (Poisson arrivals)")},
             "step_ms": [round(x, 3) for x in step_ms],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clock,

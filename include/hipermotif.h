@@ -126,6 +126,19 @@ hm_status hm_load_pattern_props(const hm_graph *g, int32_t k, int32_t mp, const 
 /* Sizes of a loaded graph (host outputs; any may be NULL). */
 hm_status hm_graph_info(const hm_graph *g, int32_t *n, int64_t *m, size_t *device_bytes);
 
+/* Bounds-checked builds (the library compiled with HM_CHECK=1,
+ * libhipermotif_check.so): every index a kernel forms into one of g's arrays
+ * (vertex records, list positions, directory entries, filter blocks, hash
+ * buckets) is tested against that array's length before the access; the
+ * first index out of range is recorded per graph and replaced by 0, so the
+ * kernel reads inside the array and runs on (no fault, no trap).  This call
+ * copies the record to *violation (HOST) and clears it: 0 = none; otherwise
+ * bit 63 set, bits 48..55 the site (1 vertex record, 2 / 3 out / in directory
+ * entry, 4 list position, 5 filter block, 6 hash bucket) and bits 0..47 the
+ * index.  Synchronises the device.  In the default build the checks are not
+ * compiled in: *violation = 0 and HM_ERR_ARG. */
+hm_status hm_check_status(const hm_graph *g, uint64_t *violation);
+
 /* Copy the built adjacency back to HOST buffers (for inspection and tests):
  * out_off/in_off int64[n+1]; out_adj/out_elab/in_adj/in_elab int32[m].
  * Any pointer may be NULL to skip that array.  Synchronous. */

@@ -28,7 +28,7 @@ from .binding import HMError, check, lib
 __all__ = ["Graph", "Pattern", "count_matches", "enumerate_matches", "count_matches_rooted",
            "count_matches_part", "enumerate_matches_part", "count_batch", "enumerate_batch", "autotune", "Server",
            "injected_states", "set_budget", "set_timing", "set_counters", "set_tuning", "get_tuning",
-           "last_stats", "MONO", "INDUCED",
+           "last_stats", "check_status", "MONO", "INDUCED",
            "HMError", "binding"]
 
 
@@ -461,6 +461,14 @@ def get_tuning() -> dict:
     t = binding.hm_tuning()
     check(lib.hm_get_tuning(ctypes.byref(t)), "hm_get_tuning")
     return t.as_dict()
+
+
+def check_status(g: Graph) -> int:
+    """The first out-of-range index the bounds-checked build recorded for g (0 = none),
+    cleared by the call; raises HMError(HM_ERR_ARG) in the default build (no checks)."""
+    w = ctypes.c_uint64()
+    check(lib.hm_check_status(g.handle, ctypes.byref(w)), "hm_check_status")
+    return int(w.value)
 
 
 def last_stats() -> dict:

@@ -2,7 +2,8 @@
 
 Sources are compiled in parallel, one translation unit per file, then linked
 into a shared library with the CUDA runtime linked statically.  Output:
-``paper_2507_04130_gb300/_build/libhipermotif.so``.
+``paper_2507_04130_gb300/_build/libhipermotif.so``; ``build(check=True)``
+makes the bounds-checked ``libhipermotif_check.so`` (HM_CHECK=1) beside it.
 """
 from __future__ import annotations
 
@@ -18,6 +19,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhipermotif.so")
+# the bounds-checked build (HM_CHECK=1): same sources, own objects
+BUILD_CHECK = os.path.join(BUILD, "check")
+LIB_CHECK = os.path.join(BUILD, "libhipermotif_check.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
@@ -34,24 +38,29 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every source for sm_103a and link the shared library; returns its path."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile every source for sm_103a and link the shared library; returns its path.
+
+    check=True builds the bounds-checked library (HM_CHECK=1) instead.
+    """
+    lib, objdir = (LIB_CHECK, BUILD_CHECK) if check else (LIB, BUILD)
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
+    defs = ["-DHM_CHECK=1"] if check else []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *COMMON, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *ARCH, *COMMON, *defs, "-c", src, "-o", obj]
         if src.endswith(".cu"):
             cmd.insert(1, "-lineinfo")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,13 +72,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = f"{LIB}.tmp{os.getpid()}"
+    tmp = f"{lib}.tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -19,7 +19,7 @@ HM_STATIC_MAX_ARCS = 3702528
 
 #: every function include/hipermotif.h declares
 EXPORTED = [
-    "hm_status_str", "hm_load_graph", "hm_free_graph", "hm_graph_info", "hm_graph_export",
+    "hm_status_str", "hm_load_graph", "hm_free_graph", "hm_graph_info", "hm_check_status", "hm_graph_export",
     "hm_graph_export_groups",
     "hm_load_pattern", "hm_free_pattern", "hm_pattern_order", "hm_count_matches",
     "hm_enumerate_matches", "hm_count_matches_rooted", "hm_count_matches_part",
@@ -98,6 +98,7 @@ _SIGS = {
     "hm_status_str": (ctypes.c_char_p, [_st]),
     "hm_load_graph": (_st, [_i32, _i64, _vp, _vp, _vp, _vp, ctypes.c_int, _vp, _pvp]),
     "hm_free_graph": (None, [_vp]),
+    "hm_check_status": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "hm_graph_info": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64),
                             ctypes.POINTER(ctypes.c_size_t)]),
     "hm_graph_export": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -140,11 +141,15 @@ _SIGS = {
 
 
 def _load():
-    path = _build.LIB
+    # HM_CHECK=1 in the environment loads the bounds-checked build instead
+    # (paper_2507_04130_gb300._build.build(check=True) makes it)
+    checked = os.environ.get("HM_CHECK", "0") == "1"
+    path = _build.LIB_CHECK if checked else _build.LIB
     if not os.path.exists(path):
         raise ImportError(
             f"{path} is missing: build the CUDA library first "
-            "(python -c 'import __graft_entry__ as g; g.build()')")
+            + ("(python -c 'from paper_2507_04130_gb300 import _build; _build.build(check=True)')" if checked
+               else "(python -c 'import __graft_entry__ as g; g.build()')"))
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)

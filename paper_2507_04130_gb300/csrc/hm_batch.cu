@@ -75,11 +75,11 @@ k_edge_seed_batch(const __grid_constant__ DevGraph G, const Plan *__restrict__ p
     int32_t first = 0, cnt = 0, a = 0, b = 0;
     int4 ia = make_int4(0, 0, 0, 0), ib = ia;
     if (e < G.m) {
-      a = __ldg(G.src + e);
-      b = __ldg(G.out_adj + e);
-      const int32_t l = __ldg(G.out_elab + e);
-      ia = __ldg(&G.vi[a]);
-      ib = __ldg(&G.vi[b]);
+      a = __ldg(G.src + HM_AT(G, e, G.m, kChkList));
+      b = __ldg(G.out_adj + HM_AT(G, e, G.m, kChkList));
+      const int32_t l = __ldg(G.out_elab + HM_AT(G, e, G.m, kChkList));
+      ia = __ldg(&G.vi[HM_AT(G, a, G.n, kChkVertex)]);
+      ib = __ldg(&G.vi[HM_AT(G, b, G.n, kChkVertex)]);
       uint32_t h = sig_hash(l, ia.x, ib.x) & T.mask;
       for (uint32_t probe = 0; probe <= T.mask; ++probe, h = (h + 1) & T.mask) {
         const SigKey k = T.keys[h];

@@ -297,6 +297,10 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
                           const int32_t *vlab, const int32_t *elab, int device_ptrs,
                           cudaStream_t s, hm_graph *g) {
   Temps T(s);
+#if HM_CHECK
+  HM_CUDA_TRY(dmalloc(&g->check, 1));  // the bounds checks' violation word
+  HM_CUDA_TRY(cudaMemsetAsync(g->check, 0, sizeof(unsigned long long), s));
+#endif
   const int32_t *d_src = src, *d_dst = dst, *d_vlab = vlab, *d_elab = elab;
   if (!device_ptrs) {
     int32_t *t;
@@ -405,7 +409,7 @@ hm_status load_graph_impl(int32_t n, int64_t m, const int32_t *src, const int32_
 void free_graph_arrays(hm_graph *g) {
   void *ptrs[] = {g->src,     g->out_adj,  g->out_elab, g->in_adj,   g->in_elab, g->vi,
                   g->off,     g->gout_adj, g->gin_adj,  g->gdir_out, g->gdir_in, g->vdir,
-                  g->afilt,   g->ahash};
+                  g->afilt,   g->ahash,    g->check};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -450,6 +454,21 @@ extern "C" void hm_free_graph(hm_graph *g) {
   free(g->vtab);
   free(g->etab);
   delete g;
+}
+
+extern "C" hm_status hm_check_status(const hm_graph *g, uint64_t *violation) {
+  if (!g || !violation) return HM_ERR_ARG;
+#if HM_CHECK
+  unsigned long long w = 0;
+  if (cudaMemcpy(&w, g->check, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(g->check, 0, sizeof(w)) != cudaSuccess)
+    return HM_ERR_CUDA;
+  *violation = w;
+  return HM_OK;
+#else
+  *violation = 0;
+  return HM_ERR_ARG;  // built without the bounds checks
+#endif
 }
 
 extern "C" hm_status hm_graph_info(const hm_graph *g, int32_t *n, int64_t *m,

@@ -59,6 +59,19 @@ struct DevGraph {
   // exact arc lookup in one or two 32-byte reads, for what the filter lets through
   const int4 *ahash;
   uint32_t ahash_nbkt;
+  // directory lengths, and the violation word of bounds-checked builds (null otherwise)
+  int64_t ndir_out, ndir_in;
+  unsigned long long *check;
+};
+
+// Sites of the bounds checks (HM_CHECK builds): which array an index was meant for.
+enum CheckSite : int {
+  kChkVertex = 1,   // vi, off, vdir (vertex id < n)
+  kChkDirOut = 2,   // gdir_out entry
+  kChkDirIn = 3,    // gdir_in entry
+  kChkList = 4,     // src, out/in adjacency and labels, grouped lists (position < m)
+  kChkFilter = 5,   // arc filter block
+  kChkHash = 6,     // arc hash bucket
 };
 
 // One pairwise condition between the position being extended (p) and an
@@ -246,19 +259,58 @@ __host__ __device__ __forceinline__ uint64_t labelled_key(uint64_t pair, int32_t
   return pair ^ (0x632be59bd9b4e019ull * ((uint64_t)(uint32_t)lab + 1));
 }
 
+// ---- bounds checks -------------------------------------------------------------
+// Built with HM_CHECK=1 (a separate library, libhipermotif_check.so), every
+// index into a graph array passes through HM_AT: one outside [0, n) is
+// recorded in *G.check -- bit 63 set, the site in bits 48..55, the index's
+// low 48 bits -- if no violation was recorded before, and replaced by 0, so
+// the access stays inside the array and the kernel runs on.  The host reads
+// and clears the word with hm_check_status.  In the default build HM_AT is
+// the index itself.
+#ifndef HM_CHECK
+#define HM_CHECK 0
+#endif
+#if HM_CHECK
+__device__ __forceinline__ int64_t checked_index(const DevGraph &G, int64_t i, int64_t n, int site) {
+  if (i >= 0 && i < n) return i;
+  if (G.check)
+    atomicCAS(G.check, 0ull,
+              (1ull << 63) | ((unsigned long long)(site & 0xff) << 48) | ((unsigned long long)i & 0xffffffffffffull));
+  return 0;
+}
+#define HM_AT(G, i, n, site) ::hm::checked_index((G), (int64_t)(i), (int64_t)(n), (site))
+#else
+#define HM_AT(G, i, n, site) (i)
+#endif
+
+// search_c over one of the graph's lists (every list array has m entries); in
+// check builds a span outside [0, m) is recorded and searched as empty
+template <bool kCount>
+__device__ __forceinline__ int32_t search_g(const DevGraph &G, const int32_t *__restrict__ a, int32_t lo,
+                                            int32_t len, int32_t x, Bytes &bytes) {
+#if HM_CHECK
+  if (len > 0 && (lo < 0 || (int64_t)lo + len > G.m)) {
+    checked_index(G, lo < 0 ? (int64_t)lo : (int64_t)lo + len - 1, G.m, kChkList);
+    return -1;
+  }
+#endif
+  return search_c<kCount>(a, lo, len, x, bytes);
+}
+
 template <bool kCount>
 __device__ __forceinline__ bool filter_has(const DevGraph &G, uint64_t h, Bytes &bytes) {
   const FilterSlot f = filter_slot_of(h, G.afilt_nblk);
+  const size_t blk = (size_t)HM_AT(G, f.blk, G.afilt_nblk, kChkFilter);
   // the block is one 32-byte sector; its first four words already reject
   // about 98 % of the keys that were never inserted, so the other four are
   // read (from the same sector, now in L1) and tested only when those pass
-  const uint4 a = __ldg(G.afilt + 2 * (size_t)f.blk);
+  const uint4 a = __ldg(G.afilt + 2 * blk);
   if (kCount) bytes += 32;
   const uint32_t x = f.bits;
   const uint32_t t = (a.x >> filter_bit(x, 0)) & (a.y >> filter_bit(x, 1)) & (a.z >> filter_bit(x, 2)) &
                      (a.w >> filter_bit(x, 3));
   if (!(t & 1u)) return false;
-  const uint4 b = __ldg(G.afilt + 2 * (size_t)f.blk + 1);
+  const uint4 b = __ldg(G.afilt + 2 * blk + 1);
   const uint32_t u = (b.x >> filter_bit(x, 4)) & (b.y >> filter_bit(x, 5)) & (b.z >> filter_bit(x, 6)) &
                      (b.w >> filter_bit(x, 7));
   return u & 1u;
@@ -286,8 +338,9 @@ __device__ __forceinline__ bool arc_find(const DevGraph &G, int32_t u, int32_t v
                                          Bytes &bytes) {
   uint32_t b = hash_bucket(pair_key(u, v), G.ahash_nbkt);
   for (uint32_t it = 0; it < G.ahash_nbkt; ++it) {
-    const int4 s0 = __ldg(G.ahash + 2 * (size_t)b);
-    const int4 s1 = __ldg(G.ahash + 2 * (size_t)b + 1);
+    const size_t bk = (size_t)HM_AT(G, b, G.ahash_nbkt, kChkHash);
+    const int4 s0 = __ldg(G.ahash + 2 * bk);
+    const int4 s1 = __ldg(G.ahash + 2 * bk + 1);
     if (kCount) bytes += 32;
     if (s0.x == u && s0.y == v) {
       *lab = s0.z;
@@ -357,6 +410,7 @@ struct hm_graph {
   int4 *ahash;
   uint32_t ahash_nbkt;
   int64_t ndir_out, ndir_in;
+  unsigned long long *check;  // bounds-checked builds: the violation word (device)
   size_t bytes;
   // multi-property graphs (hm_load_graph_props): the sorted distinct property
   // tuples of vertices and arcs (host, malloc'ed); a label is a tuple's rank
@@ -366,7 +420,7 @@ struct hm_graph {
   hm::DevGraph dev() const {
     return hm::DevGraph{n,        m,        src,     out_adj,  out_elab, in_adj,     in_elab,
                         vi,       off,      gout_adj, gin_adj, gdir_out, gdir_in,    vdir,
-                        afilt,    afilt_nblk, hm::filter_min(), ahash, ahash_nbkt};
+                        afilt,    afilt_nblk, hm::filter_min(), ahash, ahash_nbkt, ndir_out, ndir_in, check};
   }
 };
 

@@ -158,18 +158,18 @@ __device__ __forceinline__ bool arc_lookup(const DevGraph &G, int32_t x, int32_t
     return arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, lab, ctr);
   if (kC) ctr += 8;
   if (outdeg_x <= indeg_y) {
-    const int32_t o = __ldg(&G.off[x].x);
-    const int32_t i = search_c<kC>(G.out_adj, o, outdeg_x, y, ctr);
+    const int32_t o = __ldg(&G.off[HM_AT(G, x, G.n, kChkVertex)].x);
+    const int32_t i = search_g<kC>(G, G.out_adj, o, outdeg_x, y, ctr);
     if (i < 0) return false;
     if (kC) ctr += 4;
-    *lab = __ldg(G.out_elab + i);
+    *lab = __ldg(G.out_elab + HM_AT(G, i, G.m, kChkList));
     return true;
   }
-  const int32_t o = __ldg(&G.off[y].y);
-  const int32_t i = search_c<kC>(G.in_adj, o, indeg_y, x, ctr);
+  const int32_t o = __ldg(&G.off[HM_AT(G, y, G.n, kChkVertex)].y);
+  const int32_t i = search_g<kC>(G, G.in_adj, o, indeg_y, x, ctr);
   if (i < 0) return false;
   if (kC) ctr += 4;
-  *lab = __ldg(G.in_elab + i);
+  *lab = __ldg(G.in_elab + HM_AT(G, i, G.m, kChkList));
   return true;
 }
 
@@ -187,13 +187,13 @@ __device__ __forceinline__ bool seed_test(const DevGraph &G, const Plan &P, int3
   const int32_t v = P.seed_rev ? a : b;                     // image of position 1
   if (kC && (fresh || P.seed_rev)) ctr += 16;
   if (kC) ctr.model += 12;
-  const int4 iu = __ldg(&G.vi[u]);                          // Alg. 2 on u
+  const int4 iu = __ldg(&G.vi[HM_AT(G, u, G.n, kChkVertex)]);                          // Alg. 2 on u
   if (iu.x != P.vlab[0] || iu.y < P.dout[0] || iu.z < P.din[0]) return false;
   if (kC) {
     ctr += 16;
     ctr.model += 12;
   }
-  const int4 iv = __ldg(&G.vi[v]);                          // match(v, 1) + degrees
+  const int4 iv = __ldg(&G.vi[HM_AT(G, v, G.n, kChkVertex)]);                          // match(v, 1) + degrees
   if (iv.x != P.vlab[1] || iv.y < P.dout[1] || iv.z < P.din[1]) return false;
   if (root_mask && ((P.root_pos == 0 && !root_mask[u]) || (P.root_pos == 1 && !root_mask[v])))
     return false;
@@ -287,7 +287,8 @@ k_edge_seed(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P,
           ctr.model += 12;
         }
         if (e < e_end)
-          ok[j] = seed_test<kC>(G, P, G.src[e], G.out_adj[e], G.out_elab[e], root_mask, &s[j], ctr);
+          ok[j] = seed_test<kC>(G, P, G.src[HM_AT(G, e, G.m, kChkList)], G.out_adj[HM_AT(G, e, G.m, kChkList)],
+                                G.out_elab[HM_AT(G, e, G.m, kChkList)], root_mask, &s[j], ctr);
       }
     }
     const uint32_t cnt = (uint32_t)ok[0] + ok[1] + ok[2] + ok[3];
@@ -340,10 +341,10 @@ __device__ __forceinline__ bool in_nbhd(const DevGraph &G, int32_t y, int4 iy, i
                                         int32_t w, Bytes &ctr) {
   int32_t lab;
   if (iy.y && (use_filter(G, iy.y) ? arc_maybe<kC>(G, y, w, ctr) && arc_find<kC>(G, y, w, &lab, ctr)
-                                   : search_c<kC>(G.out_adj, oy.x, iy.y, w, ctr) >= 0))
+                                   : search_g<kC>(G, G.out_adj, oy.x, iy.y, w, ctr) >= 0))
     return true;
   return iy.z && (use_filter(G, iy.z) ? arc_maybe<kC>(G, w, y, ctr) && arc_find<kC>(G, w, y, &lab, ctr)
-                                      : search_c<kC>(G.in_adj, oy.y, iy.z, w, ctr) >= 0);
+                                      : search_g<kC>(G, G.in_adj, oy.y, iy.z, w, ctr) >= 0);
 }
 
 // In batched launches (kB) each seed carries its pattern id; the threshold is
@@ -365,9 +366,9 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
     const int32_t pid = kB ? pid_in[s] : 0;
     const int32_t need = kB ? plans[pid].ov_need : need_all;
     if (kC && lane == 0) ctr += 72;
-    int4 iu = __ldg(&G.vi[uv.x]), iv = __ldg(&G.vi[uv.y]);
+    int4 iu = __ldg(&G.vi[HM_AT(G, uv.x, G.n, kChkVertex)]), iv = __ldg(&G.vi[HM_AT(G, uv.y, G.n, kChkVertex)]);
     if (kC && lane == 0) ctr.model += 24 + 4ull * (iu.y + iu.z + iv.y + iv.z);  // a merge of the four lists
-    int2 ou = __ldg(&G.off[uv.x]), ov = __ldg(&G.off[uv.y]);
+    int2 ou = __ldg(&G.off[HM_AT(G, uv.x, G.n, kChkVertex)]), ov = __ldg(&G.off[HM_AT(G, uv.y, G.n, kChkVertex)]);
     // iterate the side with fewer incident arcs, probe the other
     const bool swap = (iu.y + iu.z) > (iv.y + iv.z);
     const int4 ix = swap ? iv : iu, iy = swap ? iu : iv;
@@ -378,7 +379,7 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
     for (int32_t b = 0; b < ix.y && got < need; b += 32) {
       bool hit = false;
       if (b + lane < ix.y) {
-        int32_t w = __ldg(G.out_adj + ox.x + b + lane);
+        int32_t w = __ldg(G.out_adj + HM_AT(G, (int64_t)ox.x + b + lane, G.m, kChkList));
         if (kC) ctr += 4;
         hit = in_nbhd<kC>(G, y, iy, oy, w, ctr);
       }
@@ -388,9 +389,9 @@ k_seed_overlap(const __grid_constant__ DevGraph G, int32_t need_all, const int2 
     for (int32_t b = 0; b < ix.z && got < need; b += 32) {
       bool hit = false;
       if (b + lane < ix.z) {
-        int32_t w = __ldg(G.in_adj + ox.y + b + lane);
+        int32_t w = __ldg(G.in_adj + HM_AT(G, (int64_t)ox.y + b + lane, G.m, kChkList));
         if (kC) ctr += 4;
-        bool dup = ix.y && search_c<kC>(G.out_adj, ox.x, ix.y, w, ctr) >= 0;
+        bool dup = ix.y && search_g<kC>(G, G.out_adj, ox.x, ix.y, w, ctr) >= 0;
         hit = !dup && in_nbhd<kC>(G, y, iy, oy, w, ctr);
       }
       got += __popc(__ballot_sync(kFull, hit));
@@ -471,16 +472,16 @@ __device__ __forceinline__ void set_mapped(const DevGraph &G, WarpState &S, int 
   // three independent 16-byte loads, each lane writing its own record's fields
   const bool known = c >= 0;  // c < 0: position 1 of a shared position-0 state, not yet chosen
   if (lane == 0) {
-    const int4 vi = known ? __ldg(&G.vi[c]) : make_int4(0, 0, 0, 0);
+    const int4 vi = known ? __ldg(&G.vi[HM_AT(G, c, G.n, kChkVertex)]) : make_int4(0, 0, 0, 0);
     S.map[pos] = c;
     S.deg_out[pos] = vi.y;
     S.deg_in[pos] = vi.z;
   } else if (lane == 1) {
-    const int2 o = known ? __ldg(&G.off[c]) : make_int2(0, 0);
+    const int2 o = known ? __ldg(&G.off[HM_AT(G, c, G.n, kChkVertex)]) : make_int2(0, 0);
     S.off_out[pos] = o.x;
     S.off_in[pos] = o.y;
   } else if (lane == 2) {
-    S.dir[pos] = known ? __ldg(&G.vdir[c]) : make_int4(0, 0, 0, 0);
+    S.dir[pos] = known ? __ldg(&G.vdir[HM_AT(G, c, G.n, kChkVertex)]) : make_int4(0, 0, 0, 0);
   }
 }
 
@@ -527,7 +528,7 @@ __device__ __noinline__ void write_match_rows(const Plan &P, int32_t *row_base, 
 template <bool kC>
 __device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int p, int32_t c, Bytes &ctr) {
   if (kC) ctr += 16;
-  const int4 vd = __ldg(&G.vdir[c]);
+  const int4 vd = __ldg(&G.vdir[HM_AT(G, c, G.n, kChkVertex)]);
   for (int j = 0; j < P.nla[p]; ++j) {
     const LookClass lc = P.la[p][j];
     const int4 *dir = lc.kind == kOut ? G.gdir_out : G.gdir_in;
@@ -535,7 +536,8 @@ __device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int 
     int32_t len = 0;
     for (int32_t e = 0; e < cnt; ++e) {
       if (kC) ctr += 16;
-      const int4 ent = __ldg(dir + first + e);
+      const int4 ent = __ldg(dir + HM_AT(G, (int64_t)first + e, lc.kind == kOut ? G.ndir_out : G.ndir_in,
+                                         lc.kind == kOut ? kChkDirOut : kChkDirIn));
       if (ent.x == lc.alab && ent.y == lc.vlab) {
         len = ent.w - ent.z;
         break;
@@ -548,14 +550,15 @@ __device__ __noinline__ bool lookahead_ok(const DevGraph &G, const Plan &P, int 
 
 // Find the group (arc label, vertex label) in a directory span; {first, length} or {0, 0}.
 template <bool kC>
-__device__ __forceinline__ int2 dir_lookup(const int4 *__restrict__ dir, int32_t first, int32_t cnt,
-                                           int32_t alab, int32_t vlab, int lane, Bytes &ctr) {
+__device__ __forceinline__ int2 dir_lookup(const DevGraph &G, const int4 *__restrict__ dir, int32_t first,
+                                           int32_t cnt, int32_t alab, int32_t vlab, int lane, Bytes &ctr) {
   for (int32_t b = 0; b < cnt; b += 32) {
     int4 e = make_int4(0, 0, 0, 0);
     bool hit = false;
     if (b + lane < cnt) {
       if (kC) ctr += 16;
-      e = __ldg(dir + first + b + lane);
+      e = __ldg(dir + HM_AT(G, (int64_t)first + b + lane, dir == G.gdir_out ? G.ndir_out : G.ndir_in,
+                            dir == G.gdir_out ? kChkDirOut : kChkDirIn));
       hit = e.x == alab && e.y == vlab;
     }
     const uint32_t m = __ballot_sync(kFull, hit);
@@ -579,8 +582,8 @@ __device__ __forceinline__ void setup_level(const DevGraph &G, const Plan &P, Wa
   for (int j = 0; j < P.npos[p]; ++j) {
     const Cons cs = P.cons[p][j];
     const int4 d = S.dir[cs.q];
-    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G.gdir_out, d.x, d.y, cs.lab, P.vlab[p], lane, ctr)
-                                   : dir_lookup<kC>(G.gdir_in, d.z, d.w, cs.lab, P.vlab[p], lane, ctr);
+    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G, G.gdir_out, d.x, d.y, cs.lab, P.vlab[p], lane, ctr)
+                                   : dir_lookup<kC>(G, G.gdir_in, d.z, d.w, cs.lab, P.vlab[p], lane, ctr);
     if (lane == 0) grp[P.gbase[p] + j] = r;
     if (r.y < best_len) {
       best_len = r.y;
@@ -617,7 +620,7 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
   int2 oc = make_int2(-1, -1);
   if (need_c) {
     if (kC) ctr += 16;
-    vi = __ldg(&G.vi[c]);
+    vi = __ldg(&G.vi[HM_AT(G, c, G.n, kChkVertex)]);
     if (!leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
   }
   for (int j = 0; j < nc; ++j) {
@@ -640,15 +643,15 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       } else if (rev_len < r.y) {
         if (oc.x < 0) {
           if (kC) ctr += 8;
-          oc = __ldg(&G.off[c]);
+          oc = __ldg(&G.off[HM_AT(G, c, G.n, kChkVertex)]);
         }
-        const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
-                              : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
+        const int32_t i = fwd ? search_g<kC>(G, G.in_adj, oc.y, rev_len, fq, ctr)
+                              : search_g<kC>(G, G.out_adj, oc.x, rev_len, fq, ctr);
         if (kC && i >= 0) ctr += 4;
-        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + HM_AT(G, i, G.m, kChkList)) == cs.lab;
       } else {
         const int32_t base = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
-        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, base, r.y, c, ctr) >= 0;
+        found = search_g<kC>(G, fwd ? G.gout_adj : G.gin_adj, base, r.y, c, ctr) >= 0;
       }
       if (!found) return false;
     } else {
@@ -660,13 +663,13 @@ __device__ __forceinline__ bool check_candidate(const DevGraph &G, const Plan &P
       if (use_filter(G, min(la, lb))) {
         found = arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr);
       } else if (la <= lb) {
-        found = search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) >= 0;
+        found = search_g<kC>(G, fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) >= 0;
       } else {
         if (oc.x < 0) {
           if (kC) ctr += 8;
-          oc = __ldg(&G.off[c]);
+          oc = __ldg(&G.off[HM_AT(G, c, G.n, kChkVertex)]);
         }
-        found = search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) >= 0;
+        found = search_g<kC>(G, fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) >= 0;
       }
       if (found) return false;
     }
@@ -689,7 +692,7 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
     if (kSym && (P.sym_gt[p] | P.sym_lt[p]) && !sym_ok(P, S, p, c)) return false;
   }
   if (kC) ctr += 16;
-  const int4 vi = __ldg(&G.vi[c]);
+  const int4 vi = __ldg(&G.vi[HM_AT(G, c, G.n, kChkVertex)]);
   if (base && !leaf && (vi.y < P.dout[p] || vi.z < P.din[p])) return false;
   const Cons cs = P.cons[p][j];
   const int q = cs.q;
@@ -706,14 +709,14 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
       return arc_maybe_l<kC>(G, x, y, cs.lab, ctr) && arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab;
     if (rev_len < r.y) {
       if (kC) ctr += 16;
-      const int2 oc = __ldg(&G.off[c]);
-      const int32_t i = fwd ? search_c<kC>(G.in_adj, oc.y, rev_len, fq, ctr)
-                            : search_c<kC>(G.out_adj, oc.x, rev_len, fq, ctr);
+      const int2 oc = __ldg(&G.off[HM_AT(G, c, G.n, kChkVertex)]);
+      const int32_t i = fwd ? search_g<kC>(G, G.in_adj, oc.y, rev_len, fq, ctr)
+                            : search_g<kC>(G, G.out_adj, oc.x, rev_len, fq, ctr);
       if (kC && i >= 0) ctr += 4;
-      return i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+      return i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + HM_AT(G, i, G.m, kChkList)) == cs.lab;
     }
     const int32_t lo = (fwd ? S.off_out[q] : S.off_in[q]) + r.x;
-    return search_c<kC>(fwd ? G.gout_adj : G.gin_adj, lo, r.y, c, ctr) >= 0;
+    return search_g<kC>(G, fwd ? G.gout_adj : G.gin_adj, lo, r.y, c, ctr) >= 0;
   }
   const int32_t la = fwd ? S.deg_out[q] : S.deg_in[q];
   const int32_t lb = fwd ? vi.z : vi.y;
@@ -721,10 +724,10 @@ __device__ __noinline__ bool check_one(const DevGraph &G, const Plan &P, const W
   if (kC) ctr.model += search_bytes(min(la, lb));
   if (use_filter(G, min(la, lb))) return !(arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr));
   if (la <= lb)
-    return search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
+    return search_g<kC>(G, fwd ? G.out_adj : G.in_adj, fwd ? S.off_out[q] : S.off_in[q], la, c, ctr) < 0;
   if (kC) ctr += 16;
-  const int2 oc = __ldg(&G.off[c]);
-  return search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) < 0;
+  const int2 oc = __ldg(&G.off[HM_AT(G, c, G.n, kChkVertex)]);
+  return search_g<kC>(G, fwd ? G.in_adj : G.out_adj, fwd ? oc.y : oc.x, lb, fq, ctr) < 0;
 }
 
 // ---- last-level flattening ---------------------------------------------------
@@ -749,8 +752,8 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
   const int L = p - 1;
   const int nc = P.ncons[p];
   if (kC) ctr += 32;
-  const int4 vi = __ldg(&G.vi[d]);
-  const int2 od = __ldg(&G.off[d]);
+  const int4 vi = __ldg(&G.vi[HM_AT(G, d, G.n, kChkVertex)]);
+  const int2 od = __ldg(&G.off[HM_AT(G, d, G.n, kChkVertex)]);
   for (int j = 0; j < nc; ++j) {
     if (j == drive) continue;
     const Cons cs = P.cons[p][j];
@@ -767,12 +770,12 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
       if (kC) ctr.model += search_bytes(min(rev_len, r.y));
       bool found;
       if (rev_len < r.y) {
-        const int32_t i = fwd ? search_c<kC>(G.in_adj, od.y, rev_len, fq, ctr)
-                              : search_c<kC>(G.out_adj, od.x, rev_len, fq, ctr);
+        const int32_t i = fwd ? search_g<kC>(G, G.in_adj, od.y, rev_len, fq, ctr)
+                              : search_g<kC>(G, G.out_adj, od.x, rev_len, fq, ctr);
         if (kC && i >= 0) ctr += 4;
-        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + i) == cs.lab;
+        found = i >= 0 && __ldg((fwd ? G.in_elab : G.out_elab) + HM_AT(G, i, G.m, kChkList)) == cs.lab;
       } else {
-        found = search_c<kC>(fwd ? G.gout_adj : G.gin_adj, (fwd ? q_off_out : q_off_in) + r.x, r.y,
+        found = search_g<kC>(G, fwd ? G.gout_adj : G.gin_adj, (fwd ? q_off_out : q_off_in) + r.x, r.y,
                              d, ctr) >= 0;
       }
       if (!found) return false;
@@ -782,8 +785,8 @@ __device__ __noinline__ bool check_leaf_searched(const DevGraph &G, const Plan &
       if (la == 0 || lb == 0) continue;
       if (kC) ctr.model += search_bytes(min(la, lb));
       const bool found =
-          la <= lb ? search_c<kC>(fwd ? G.out_adj : G.in_adj, fwd ? q_off_out : q_off_in, la, d, ctr) >= 0
-                   : search_c<kC>(fwd ? G.in_adj : G.out_adj, fwd ? od.y : od.x, lb, fq, ctr) >= 0;
+          la <= lb ? search_g<kC>(G, fwd ? G.out_adj : G.in_adj, fwd ? q_off_out : q_off_in, la, d, ctr) >= 0
+                   : search_g<kC>(G, fwd ? G.in_adj : G.out_adj, fwd ? od.y : od.x, lb, fq, ctr) >= 0;
       if (found) return false;
     }
   }
@@ -844,7 +847,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
         const bool found =
             use_filter(G, r.y)
                 ? arc_find<kC>(G, x, y, &lab, ctr) && lab == cs.lab
-                : search_c<kC>(fwd ? G.gout_adj : G.gin_adj,
+                : search_g<kC>(G, fwd ? G.gout_adj : G.gin_adj,
                                (fwd ? (mine ? o.off_out : S.off_out[q]) : (mine ? o.off_in : S.off_in[q])) + r.x,
                                r.y, d, ctr) >= 0;
         if (!found) return false;
@@ -853,7 +856,7 @@ __device__ __forceinline__ bool check_leaf(const DevGraph &G, const Plan &P, con
         const bool found =
             use_filter(G, la)
                 ? arc_find<kC>(G, x, y, &lab, ctr)
-                : search_c<kC>(fwd ? G.out_adj : G.in_adj,
+                : search_g<kC>(G, fwd ? G.out_adj : G.in_adj,
                                fwd ? (mine ? o.off_out : S.off_out[q]) : (mine ? o.off_in : S.off_in[q]), la, d,
                                ctr) >= 0;
         if (found) return false;
@@ -881,7 +884,7 @@ __device__ __forceinline__ bool arc_exists(const DevGraph &G, int32_t x, int32_t
   int32_t lab;
   if (G.filt_min >= 0) return arc_maybe<kC>(G, x, y, ctr) && arc_find<kC>(G, x, y, &lab, ctr);
   if (kC) ctr += 32;
-  const int4 ix = __ldg(&G.vi[x]), iy = __ldg(&G.vi[y]);
+  const int4 ix = __ldg(&G.vi[HM_AT(G, x, G.n, kChkVertex)]), iy = __ldg(&G.vi[HM_AT(G, y, G.n, kChkVertex)]);
   return arc_lookup<kC>(G, x, y, ix.y, iy.z, &lab, ctr);
 }
 
@@ -990,8 +993,8 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
     const Cons cs = P.cons[p][j];
     if (cs.q == L) continue;
     const int4 dq = S.dir[cs.q];
-    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G.gdir_out, dq.x, dq.y, cs.lab, P.vlab[p], lane, ctr)
-                                   : dir_lookup<kC>(G.gdir_in, dq.z, dq.w, cs.lab, P.vlab[p], lane, ctr);
+    const int2 r = cs.kind == kOut ? dir_lookup<kC>(G, G.gdir_out, dq.x, dq.y, cs.lab, P.vlab[p], lane, ctr)
+                                   : dir_lookup<kC>(G, G.gdir_in, dq.z, dq.w, cs.lab, P.vlab[p], lane, ctr);
     if (lane == 0) grp[P.gbase[p] + j] = r;
     dead |= r.y == 0;
   }
@@ -1009,10 +1012,10 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
   int32_t drv_j = 0, drv_lo = 0, drv_len = 0, drv_kind = 0;
   int4 probe = make_int4(0, 0, 0, 0);
   if (mine) {
-    const int32_t c = __ldg(adj + base + lane);
-    const int4 vi = __ldg(&G.vi[c]);
-    const int2 of = __ldg(&G.off[c]);
-    const int4 vd = __ldg(&G.vdir[c]);
+    const int32_t c = __ldg(adj + HM_AT(G, (int64_t)base + lane, G.m, kChkList));
+    const int4 vi = __ldg(&G.vi[HM_AT(G, c, G.n, kChkVertex)]);
+    const int2 of = __ldg(&G.off[HM_AT(G, c, G.n, kChkVertex)]);
+    const int4 vd = __ldg(&G.vdir[HM_AT(G, c, G.n, kChkVertex)]);
     if (kC) ctr += 52;
     o.c = c;
     o.off_out = of.x;
@@ -1034,7 +1037,10 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
           int4 ent[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t)
-            ent[t] = e0 + t < cnt ? __ldg(dir + first + e0 + t) : make_int4(0, 0, 0, 0);
+            ent[t] = e0 + t < cnt ? __ldg(dir + HM_AT(G, (int64_t)first + e0 + t,
+                                                     cs.kind == kOut ? G.ndir_out : G.ndir_in,
+                                                     cs.kind == kOut ? kChkDirOut : kChkDirIn))
+                                  : make_int4(0, 0, 0, 0);
           if (kC) ctr += 16 * (uint64_t)min(4, cnt - e0);
 #pragma unroll
           for (int t = 0; t < 4; ++t)
@@ -1107,7 +1113,7 @@ __device__ uint32_t leaf_flatten(const DevGraph &G, const Plan &P, WarpState &S,
       ctr += 4;
       ctr.model += 8;
     }
-    return __ldg((od.z == kOut ? G.gout_adj : G.gin_adj) + od.y + (g - od.w));
+    return __ldg((od.z == kOut ? G.gout_adj : G.gin_adj) + HM_AT(G, (int64_t)od.y + (g - od.w), G.m, kChkList));
   };
   // the next chunk's owners and candidates are fetched while this chunk is checked
   int ow_next = owner_of(lane);
@@ -1599,7 +1605,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
           const int ci = lane / J, slot = lane - ci * J;
           bool pass = false;
           if (ci < take && ((allow >> ci) & 1u)) {
-            const int32_t cc = __ldg(adj + lo + ci);
+            const int32_t cc = __ldg(adj + HM_AT(G, (int64_t)lo + ci, G.m, kChkList));
             if (kC && slot == 0) {
               ctr += 4;
               ctr.model += 8;
@@ -1615,13 +1621,13 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
             if (((bal >> (i * J)) & need) == need) m |= 1u << i;
           if (lane < take && ((m >> lane) & 1u)) {
             ok = true;
-            c = __ldg(adj + lo + lane);
+            c = __ldg(adj + HM_AT(G, (int64_t)lo + lane, G.m, kChkList));
           }
         } else {
           take = 32;
           const int32_t idx = lo + lane;
           if (idx < hi && ((allow >> lane) & 1u)) {
-            c = __ldg(adj + idx);
+            c = __ldg(adj + HM_AT(G, idx, G.m, kChkList));
             if (kC) {
               ctr += 4;
               ctr.model += 8;
@@ -1696,7 +1702,7 @@ k_extend(const __grid_constant__ DevGraph G, const __grid_constant__ Plan P0,
       const int b = __ffs(m) - 1;
       const Cons dc = P.cons[level][S.drive[level]];
       const int32_t *adj = dc.kind == kOut ? G.gout_adj : G.gin_adj;
-      const int32_t c = __ldg(adj + S.base[level] + b);
+      const int32_t c = __ldg(adj + HM_AT(G, (int64_t)S.base[level] + b, G.m, kChkList));
       __syncwarp();
       if (lane == 0) S.mask[level] = m & (m - 1);
       if (kC && lane == 0) ctr += 4;
