@@ -31,7 +31,10 @@
 //                   budget.  With a pendant position 1 the seeds of one
 //                   position-0 image (induced: at most 32 of them) share one
 //                   search, and position 1 is chosen at the leaves
-//                   (expand_position1).
+//                   (expand_position1).  A pattern with label-preserving
+//                   automorphisms is searched for one map per orbit (order
+//                   constraints between images) and each map found is
+//                   written with its automorphic images.
 //   k_seed_rows     two-vertex patterns: each seed is already a match.
 //
 // Output: a match count (uint64), and optionally rows in original pattern
