@@ -649,19 +649,42 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort4_fused(const __grid_co
     //    small one, where that would leave few blocks scanning many digits
     //    one after another, one warp per digit
     if (grid >= kWarpScanBelow) {
+      // each thread takes up to four consecutive blocks' counts, so one
+      // block-wide scan covers a grid of up to 1,024 blocks
+      const int per = (grid + kSortThreads - 1) / kSortThreads;
       for (int d = b; d < kRadix; d += grid) {
         const uint32_t *h = F.hist + (int64_t)d * grid;
         uint32_t *q = F.part + (int64_t)d * grid;
-        uint32_t run = 0;
-        for (int c0 = 0; c0 < grid; c0 += blockDim.x) {
-          const int c = c0 + threadIdx.x;
-          const uint32_t v = c < grid ? __ldcg(h + c) : 0u;
-          uint32_t chunk;
-          const uint32_t before = block_excl_scan(v, &chunk);
-          if (c < grid) q[c] = run + before;
-          run += chunk;
+        if (per <= 4) {
+          const int c0 = threadIdx.x * per;
+          uint32_t v[4] = {0u, 0u, 0u, 0u}, sum = 0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (t < per && c0 + t < grid) {
+              v[t] = __ldcg(h + c0 + t);
+              sum += v[t];
+            }
+          uint32_t all;
+          uint32_t run = block_excl_scan(sum, &all);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (t < per && c0 + t < grid) {
+              q[c0 + t] = run;
+              run += v[t];
+            }
+          if (threadIdx.x == 0) F.tot[d] = all;
+        } else {
+          uint32_t run = 0;
+          for (int c0 = 0; c0 < grid; c0 += blockDim.x) {
+            const int c = c0 + threadIdx.x;
+            const uint32_t v = c < grid ? __ldcg(h + c) : 0u;
+            uint32_t chunk;
+            const uint32_t before = block_excl_scan(v, &chunk);
+            if (c < grid) q[c] = run + before;
+            run += chunk;
+          }
+          if (threadIdx.x == 0) F.tot[d] = run;
         }
-        if (threadIdx.x == 0) F.tot[d] = run;
       }
     } else {
       const int lane = threadIdx.x & 31, nw = grid * kSortWarps;
